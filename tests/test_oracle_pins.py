@@ -1,0 +1,425 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: each check uses a hand-derived
+fixture, a closed form, an invariant, a library routine the oracle does not
+call for that step (SVD norm, HiGHS), or brute force on tiny inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.optimize import linprog
+
+import lpgen
+import oracle
+from oracle.pdhg import Scaled, State
+from tests.conftest import arr, load_golden
+
+SENSE = {"E": ord("E"), "L": ord("L"), "G": ord("G")}
+
+
+def _scaled_from_dense(A, b, c, l, u, sense, dr=None, dc=None):
+    """Build the oracle's preprocessed-problem object for a given (A, b, c, l, u)
+    and explicit diagonal factors (identity by default)."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    dr = np.ones(m) if dr is None else np.asarray(dr, dtype=np.float64)
+    dc = np.ones(n) if dc is None else np.asarray(dc, dtype=np.float64)
+    As = sp.csr_matrix(np.diag(dr) @ A @ np.diag(dc))
+    with np.errstate(invalid="ignore"):
+        return Scaled(
+            A=As, At=As.T.tocsr(), b=dr * np.asarray(b, float), c=dc * np.asarray(c, float),
+            l=np.asarray(l, float) / dc, u=np.asarray(u, float) / dc,
+            sense=np.array([SENSE[s] for s in sense], dtype=np.uint8), dr=dr, dc=dc,
+            b_norm=float(np.linalg.norm(b)), c_norm=float(np.linalg.norm(c)),
+        )
+
+
+def _highs(lp):
+    """Optimal objective of an lpgen.LP by HiGHS (scipy)."""
+    A = lp.csr().toarray()
+    ub_rows, ub_rhs, eq_rows, eq_rhs = [], [], [], []
+    for i in range(lp.m):
+        s = lp.sense[i]
+        if s == SENSE["E"]:
+            eq_rows.append(A[i]); eq_rhs.append(lp.b[i])
+        elif s == SENSE["L"]:
+            ub_rows.append(A[i]); ub_rhs.append(lp.b[i])
+        else:
+            ub_rows.append(-A[i]); ub_rhs.append(-lp.b[i])
+    bounds = [(None if not np.isfinite(lo) else lo, None if not np.isfinite(hi) else hi)
+              for lo, hi in zip(lp.lb, lp.ub)]
+    res = linprog(lp.c, A_ub=np.array(ub_rows) if ub_rows else None, b_ub=ub_rhs or None,
+                  A_eq=np.array(eq_rows) if eq_rows else None, b_eq=eq_rhs or None,
+                  bounds=bounds, method="highs")
+    assert res.status == 0, res.message
+    return res.fun
+
+
+# ---------------------------------------------------------------------------
+# Hand-derived one-step example (tests/golden/one_step_1x2.json)
+# ---------------------------------------------------------------------------
+
+def test_golden_two_steps_by_hand():
+    g = load_golden("one_step_1x2.json")
+    L = g["lp"]
+    P = _scaled_from_dense(L["A"], L["b"], L["c"], arr(L["l"]), arr(L["u"]), L["sense"])
+    eta, omega = g["start"]["eta"], g["start"]["omega"]
+    x = arr(g["start"]["x"]); y = arr(g["start"]["y"]); ax = P.A @ x
+    T = np.ones(2); Sig = np.ones(1)
+    for key in ("step1", "step2"):
+        e = g[key]
+        x1, gg, xh = oracle.primal_half_step(P, x, y, T, eta, omega)
+        y1, ax1, r, yh = oracle.dual_half_step(P, x1, y, ax, Sig, eta, omega)
+        np.testing.assert_allclose(gg, e["g"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(xh, e["x_half"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(x1, e["x"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(ax1, e["ax"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(r, e["r"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(yh, e["y_half"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(y1, e["y"], rtol=0, atol=1e-15)
+        gT, gS = oracle.online_gradients(P, gg, xh, ax, r, yh, eta, omega, normalize=False)
+        np.testing.assert_allclose(gT, e["grad_T"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(gS, e["grad_Sigma"], rtol=0, atol=1e-15)
+        lim = oracle.step_size_limit(x1 - x, y1 - y, ax1 - ax, T, Sig, omega)
+        if e["eta_max"] == "inf":
+            assert lim == math.inf
+        else:
+            assert lim == pytest.approx(e["eta_max"], rel=1e-15)
+        if key == "step2":
+            gTn, gSn = oracle.online_gradients(P, gg, xh, ax, r, yh, eta, omega, normalize=True)
+            np.testing.assert_allclose(gTn, e["grad_T_normalized"], rtol=1e-15)
+            np.testing.assert_allclose(gSn, e["grad_Sigma_normalized"], rtol=1e-15)
+            o = oracle.Options(alpha=e["adagrad_alpha"], scheduler="adagrad")
+            Tn, _, _ = oracle.ogd_update(T, np.zeros(2), 0.0, gT, o)
+            Sn, _, _ = oracle.ogd_update(Sig, np.zeros(1), 0.0, gS, o)
+            np.testing.assert_allclose(Tn, e["T_after"], rtol=1e-15)
+            np.testing.assert_allclose(Sn, e["Sigma_after"], rtol=1e-15)
+        x, y, ax = x1, y1, ax1
+
+
+def test_golden_plain_attempts_match_hand_steps():
+    """Two plain-mode attempts from the hand example's start reproduce its iterates."""
+    g = load_golden("one_step_1x2.json")
+    L = g["lp"]
+    P = _scaled_from_dense(L["A"], L["b"], L["c"], arr(L["l"]), arr(L["u"]), L["sense"])
+    S = State(x=np.zeros(2), y=np.zeros(1), ax=np.zeros(1), T=np.ones(2), Sigma=np.ones(1),
+              GT=np.zeros(2), GS=np.zeros(1), GT_norm=0.0, GS_norm=0.0, eta=0.5, omega=1.0,
+              xbar=np.zeros(2), ybar=np.zeros(1))
+    o = oracle.Options(mode="plain", alpha=0.0, phi=0)
+    for key in ("step1", "step2"):
+        assert oracle.attempt(P, S, o)
+        np.testing.assert_allclose(S.x, g[key]["x"], atol=1e-15)
+        np.testing.assert_allclose(S.y, g[key]["y"], atol=1e-15)
+    # pdlp mode rejects the second step at eta = 0.5 (limit 13/27)
+    S2 = State(x=np.zeros(2), y=np.array([1.5]), ax=np.zeros(1), T=np.ones(2), Sigma=np.ones(1),
+               GT=np.zeros(2), GS=np.zeros(1), GT_norm=0.0, GS_norm=0.0, eta=0.5, omega=1.0,
+               xbar=np.zeros(2), ybar=np.zeros(1), k=1, attempts=1)
+    assert not oracle.attempt(P, S2, oracle.Options(mode="pdlp", phi=0))
+    np.testing.assert_array_equal(S2.x, [0.0, 0.0])
+    assert S2.k == 1 and S2.attempts == 2
+    t = 2
+    expect_eta = min((1 - (t + 1) ** -0.3) * 13 / 27, (1 + (t + 1) ** -0.6) * 0.5)
+    assert S2.eta == pytest.approx(expect_eta, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# KKT definition (tests/golden/kkt_2x3.json)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scaled", [False, True])
+def test_golden_kkt_by_hand(scaled):
+    g = load_golden("kkt_2x3.json")
+    dr = np.array([0.5, 3.0]) if scaled else None
+    dc = np.array([2.0, 0.25, 7.0]) if scaled else None
+    P = _scaled_from_dense(g["A"], g["b"], g["c"], arr(g["l"]), arr(g["u"]), g["sense"], dr, dc)
+    x = arr(g["x"]) / P.dc  # the point in scaled coordinates
+    y = arr(g["y"]) / P.dr
+    k = oracle.kkt(P, x, y, P.A @ x, P.At @ y)
+    e = g["expect"]
+    for key in ("pobj", "dobj", "pres_norm", "dres_norm", "rel_pres", "rel_dres", "rel_gap"):
+        assert k[key] == pytest.approx(e[key], rel=1e-14, abs=1e-15), key
+    if not scaled:
+        np.testing.assert_allclose(k["parts"], e["parts"], rtol=1e-14)
+
+
+def test_kkt_zero_at_constructed_optimum():
+    for lp in (lpgen.tiny_random(3), lpgen.mixed_small(2)):
+        o = oracle.Options()
+        P = oracle.scale_problem(lp, o)
+        x = lp.x_opt / P.dc
+        y = lp.y_opt / P.dr
+        k = oracle.kkt(P, x, y, P.A @ x, P.At @ y)
+        assert k["rel_pres"] < 1e-12 and k["rel_dres"] < 1e-12 and k["rel_gap"] < 1e-12
+        # a perturbed point is not optimal
+        k2 = oracle.kkt(P, x * 1.01, y, P.A @ (x * 1.01), P.At @ y)
+        assert max(k2["rel_pres"], k2["rel_gap"]) > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Online gradients: finite differences of the losses of Eq. (5)
+# ---------------------------------------------------------------------------
+
+def _random_state(P, rng):
+    m, n = P.A.shape
+    lo = np.where(np.isfinite(P.l), P.l, -5.0)
+    hi = np.where(np.isfinite(P.u), P.u, 5.0)
+    x = lo + (hi - lo) * rng.random(n)
+    y = oracle.pdhg.project_dual(P, rng.standard_normal(m))
+    return x, y
+
+
+def test_online_gradients_match_finite_differences():
+    rng = np.random.default_rng(7)
+    lp = lpgen.mixed_small(5, m=20, n=40)
+    P = oracle.scale_problem(lp, oracle.Options())
+    x, y = _random_state(P, rng)
+    ax = P.A @ x
+    T = 0.5 + rng.random(P.A.shape[1])
+    Sig = 0.5 + rng.random(P.A.shape[0])
+    eta, omega = 0.7, 1.3
+
+    def x_next(Tv):
+        return oracle.primal_half_step(P, x, y, Tv, eta, omega)[0]
+
+    def y_next(Sv, xn):
+        return oracle.dual_half_step(P, xn, y, ax, Sv, eta, omega)[0]
+
+    x1, g, xh = oracle.primal_half_step(P, x, y, T, eta, omega)
+    y1, ax1, r, yh = oracle.dual_half_step(P, x1, y, ax, Sig, eta, omega)
+    gT, gS = oracle.online_gradients(P, g, xh, ax, r, yh, eta, omega, normalize=False)
+    gTn, gSn = oracle.online_gradients(P, g, xh, ax, r, yh, eta, omega, normalize=True)
+    L0 = oracle.lagrangian(P, x, y)
+    h = 1e-6
+    checked_p = checked_d = 0
+    for j in range(P.A.shape[1]):
+        # skip coordinates within h of a projection kink
+        step = (eta / omega) * g[j]
+        if np.isfinite(P.l[j]) and abs(xh[j] - P.l[j]) < 2 * h * abs(step) + 1e-9:
+            continue
+        if np.isfinite(P.u[j]) and abs(xh[j] - P.u[j]) < 2 * h * abs(step) + 1e-9:
+            continue
+        Tp = T.copy(); Tp[j] += h
+        Tm = T.copy(); Tm[j] -= h
+        lp_ = oracle.lagrangian(P, x_next(Tp), y) - L0
+        lm_ = oracle.lagrangian(P, x_next(Tm), y) - L0
+        fd = (lp_ - lm_) / (2 * h)
+        assert fd == pytest.approx(gT[j], rel=1e-5, abs=1e-8)
+        checked_p += 1
+    for i in range(P.A.shape[0]):
+        step = eta * omega * r[i]
+        if P.sense[i] != ord("E") and abs(yh[i]) < 2 * h * abs(step) + 1e-9:
+            continue
+        Sp = Sig.copy(); Sp[i] += h
+        Sm = Sig.copy(); Sm[i] -= h
+        # l^d(Sigma) = L(x^k, y^k) - L(x^k, y^{k+1}(Sigma))
+        lp_ = L0 - oracle.lagrangian(P, x, y_next(Sp, x1))
+        lm_ = L0 - oracle.lagrangian(P, x, y_next(Sm, x1))
+        fd = (lp_ - lm_) / (2 * h)
+        assert fd == pytest.approx(gS[i], rel=1e-5, abs=1e-8)
+        checked_d += 1
+    assert checked_p > 20 and checked_d > 10
+    np.testing.assert_allclose(gTn, gT / float(g @ g), rtol=1e-14)
+    res = P.b - ax
+    np.testing.assert_allclose(gSn, gS / float(res @ res), rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Invariants of the preconditioner update
+# ---------------------------------------------------------------------------
+
+def test_alpha_zero_is_vanilla_bitwise():
+    """A zero learning rate reproduces the run without any update, bit for bit."""
+    lp = lpgen.mixed_small(3)
+    for mode in ("pdlp", "plain"):
+        runs = []
+        for phi in (1, 0):
+            trace = []
+            o = oracle.Options(mode=mode, alpha=0.0, phi=phi, normalize=True)
+            oracle.solve(lp, o, tol=1e-12, iter_limit=300,
+                         trace=lambda P, S: trace.append((S.x.copy(), S.y.copy(), S.T.copy(), S.Sigma.copy(), S.eta)))
+            runs.append(trace)
+        for a, b in zip(*runs):
+            for u, v in zip(a[:4], b[:4]):
+                assert np.array_equal(u, v)
+            assert a[4] == b[4]
+            assert np.all(a[2] == 1.0) and np.all(a[3] == 1.0)
+
+
+@pytest.mark.parametrize("scheduler", ["adagrad", "adagrad_norm", "const"])
+def test_T_monotone_and_sigma_floor(scheduler):
+    lp = lpgen.mixed_small(4)
+    prev = {}
+    floor = 1e-6
+    seen_floor = [False]
+
+    def tr(P, S):
+        if "T" in prev:
+            assert np.all(S.T >= prev["T"])
+        assert np.all(S.Sigma >= floor) and np.all(S.T >= floor)
+        if np.any(S.Sigma == floor):
+            seen_floor[0] = True
+        prev["T"] = S.T.copy()
+
+    alpha = 0.5 if scheduler == "const" else 5.0
+    o = oracle.Options(alpha=alpha, phi=1, scheduler=scheduler, normalize=True)
+    oracle.solve(lp, o, tol=1e-12, iter_limit=400, trace=tr)
+    assert np.all(np.isfinite(prev["T"]))
+    if scheduler != "const":
+        assert seen_floor[0], "a large learning rate should drive some Sigma_i to the floor"
+
+
+def test_step_limit_lower_bound():
+    """eta_max >= 1 / ||Sigma^1/2 A T^1/2||_2 for any (dx, dy): Cauchy-Schwarz
+    plus the AM-GM inequality, for every positive T, Sigma and omega."""
+    rng = np.random.default_rng(11)
+    A = sp.random(30, 50, density=0.2, random_state=3, format="csr")
+    for _ in range(200):
+        T = np.exp(rng.normal(size=50))
+        Sig = np.exp(rng.normal(size=30))
+        omega = float(np.exp(rng.normal()))
+        dx = rng.normal(size=50)
+        dy = rng.normal(size=30)
+        lim = oracle.step_size_limit(dx, dy, A @ dx, T, Sig, omega)
+        M = np.diag(np.sqrt(Sig)) @ A.toarray() @ np.diag(np.sqrt(T))
+        assert lim * np.linalg.norm(M, 2) >= 1.0 - 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Preprocessing
+# ---------------------------------------------------------------------------
+
+def test_ruiz_equilibrates_infinity_norms():
+    rng = np.random.default_rng(0)
+    A = sp.random(80, 120, density=0.1, random_state=1, format="csr")
+    A.data = 10.0 ** rng.uniform(-3, 3, size=A.nnz) * np.sign(rng.normal(size=A.nnz))
+    keep_r = np.diff(A.indptr) > 0
+    keep_c = np.bincount(A.indices, minlength=120) > 0
+    As, dr, dc = oracle.ruiz_equilibrate(A, 40)
+    rmax = abs(As).max(axis=1).toarray().ravel()
+    cmax = abs(As).max(axis=0).toarray().ravel()
+    np.testing.assert_allclose(rmax[keep_r], 1.0, atol=1e-6)
+    np.testing.assert_allclose(cmax[keep_c], 1.0, atol=1e-6)
+    np.testing.assert_allclose(As.toarray(), np.diag(dr) @ A.toarray() @ np.diag(dc), rtol=1e-12, atol=0)
+
+
+def test_pock_chambolle_norm_at_most_one():
+    rng = np.random.default_rng(1)
+    for s in range(5):
+        A = sp.random(40, 60, density=0.15, random_state=s, format="csr")
+        A.data = rng.normal(size=A.nnz)
+        As, fr, fc = oracle.pock_chambolle_rescale(A, 1.0)
+        assert np.linalg.norm(As.toarray(), 2) <= 1.0 + 1e-12
+        np.testing.assert_allclose(As.toarray(), np.diag(fr) @ A.toarray() @ np.diag(fc), rtol=1e-13)
+
+
+def test_l2_rescale_closed_forms():
+    # a diagonal matrix becomes the identity up to sign
+    d = np.array([4.0, -9.0, 0.25])
+    As, fr, fc = oracle.l2_norm_rescale(sp.csr_matrix(np.diag(d)))
+    np.testing.assert_allclose(As.toarray(), np.diag(np.sign(d)), rtol=1e-15)
+    # a rank-one positive matrix u v^T maps to sqrt(u_i v_j) / sqrt(||u|| ||v||)
+    u = np.array([1.0, 2.0, 3.0]); v = np.array([4.0, 1.0])
+    As, _, _ = oracle.l2_norm_rescale(sp.csr_matrix(np.outer(u, v)))
+    expect = np.sqrt(np.outer(u, v)) / math.sqrt(np.linalg.norm(u) * np.linalg.norm(v))
+    np.testing.assert_allclose(As.toarray(), expect, rtol=1e-14)
+
+
+def test_power_iteration_matches_svd():
+    rng = np.random.default_rng(2)
+    A = sp.random(50, 70, density=0.2, random_state=4, format="csr")
+    A.data = rng.normal(size=A.nnz)
+    est = oracle.power_spectral_norm(A, 200)
+    assert est == pytest.approx(np.linalg.norm(A.toarray(), 2), rel=1e-8)
+
+
+def test_scaling_preserves_the_optimum():
+    """The rescaled LP (mapped back) has the same optimum: HiGHS on both."""
+    lp = lpgen.mixed_small(6, m=25, n=50)
+    for mode in ("pdlp", "plain"):
+        P = oracle.scale_problem(lp, oracle.Options(mode=mode))
+        scaled = lpgen.LP(
+            m=lp.m, n=lp.n, row_ptr=P.A.indptr.astype(np.int64), col_idx=P.A.indices.astype(np.int32),
+            val=P.A.data, b=P.b, c=P.c, lb=P.l, ub=P.u, sense=lp.sense)
+        assert _highs(scaled) == pytest.approx(_highs(lp), rel=1e-9, abs=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Converged solutions: brute force, constructed optimum, HiGHS
+# ---------------------------------------------------------------------------
+
+def test_vertex_enumeration_agrees_with_highs():
+    rng = np.random.default_rng(5)
+    for trial in range(10):
+        m, n = int(rng.integers(1, 4)), int(rng.integers(2, 6))
+        lp = _tiny_box_lp(rng, m, n)
+        v, _ = oracle.enumerate_vertices(lp.csr().toarray(), lp.b, lp.c, lp.lb, lp.ub, lp.sense)
+        assert v == pytest.approx(_highs(lp), rel=1e-9, abs=1e-9)
+
+
+def _tiny_box_lp(rng, m, n):
+    """A tiny feasible LP with finite boxes and random senses (feasible at a random point)."""
+    A = rng.normal(size=(m, n))
+    x0 = rng.uniform(0, 3, size=n)
+    senses = rng.choice([ord("E"), ord("L"), ord("G")], size=m).astype(np.uint8)
+    b = A @ x0 + np.where(senses == ord("L"), 0.5, np.where(senses == ord("G"), -0.5, 0.0))
+    Asp = sp.csr_matrix(A)
+    return lpgen.LP(m=m, n=n, row_ptr=Asp.indptr.astype(np.int64), col_idx=Asp.indices.astype(np.int32),
+                    val=Asp.data.astype(float), b=b, c=rng.normal(size=n), lb=np.zeros(n),
+                    ub=np.full(n, 3.0), sense=senses)
+
+
+@pytest.mark.parametrize("mode", ["pdlp", "plain"])
+def test_oracle_reaches_vertex_optimum(mode):
+    rng = np.random.default_rng(9)
+    for trial in range(8):
+        m, n = int(rng.integers(1, 5)), int(rng.integers(2, 7))
+        lp = _tiny_box_lp(rng, m, n)
+        v, _ = oracle.enumerate_vertices(lp.csr().toarray(), lp.b, lp.c, lp.lb, lp.ub, lp.sense)
+        res, _, _ = oracle.solve(lp, oracle.Options(mode=mode, alpha=1e-2, phi=1), tol=1e-9, iter_limit=400_000)
+        assert res.status == oracle.pdhg.OPTIMAL
+        assert res.pobj == pytest.approx(v, rel=1e-6, abs=1e-6)
+
+
+def test_golden_two_variable_lp():
+    g = load_golden("lp_2var.json")
+    Asp = sp.csr_matrix(np.array(g["A"]))
+    lp = lpgen.LP(m=2, n=2, row_ptr=Asp.indptr.astype(np.int64), col_idx=Asp.indices.astype(np.int32),
+                  val=Asp.data, b=arr(g["b"]), c=arr(g["c"]), lb=arr(g["l"]), ub=arr(g["u"]),
+                  sense=np.array([SENSE[s] for s in g["sense"]], dtype=np.uint8))
+    for mode in ("pdlp", "plain"):
+        res, _, _ = oracle.solve(lp, oracle.Options(mode=mode, alpha=1e-2, phi=1), tol=1e-10, iter_limit=200_000)
+        assert res.status == oracle.pdhg.OPTIMAL
+        assert res.pobj == pytest.approx(g["obj_opt"], rel=1e-8)
+        np.testing.assert_allclose(res.x, g["x_opt"], atol=1e-7)
+        np.testing.assert_allclose(res.y, g["y_opt"], atol=1e-7)
+
+
+@pytest.mark.parametrize("mode,alpha,phi", [("plain", 0.0, 1), ("plain", 1e-2, 1), ("pdlp", 0.0, 20), ("pdlp", 1e-3, 20)])
+def test_tiny_random_reaches_constructed_optimum(mode, alpha, phi):
+    lp = lpgen.tiny_random(0)
+    res, _, _ = oracle.solve(lp, oracle.Options(mode=mode, alpha=alpha, phi=phi), tol=1e-8, iter_limit=200_000)
+    assert res.status == oracle.pdhg.OPTIMAL
+    assert res.pobj == pytest.approx(lp.obj_opt, rel=1e-7)
+    assert res.dobj == pytest.approx(lp.obj_opt, rel=1e-7)
+
+
+def test_mixed_senses_and_bounds_match_highs():
+    for seed in range(3):
+        lp = lpgen.mixed_small(seed)
+        ref = _highs(lp)
+        assert ref == pytest.approx(lp.obj_opt, rel=1e-7, abs=1e-7)
+        res, _, _ = oracle.solve(lp, oracle.Options(alpha=1e-3), tol=1e-8, iter_limit=200_000)
+        assert res.status == oracle.pdhg.OPTIMAL
+        assert res.pobj == pytest.approx(ref, rel=1e-6, abs=1e-6)
+
+
+def test_small_transport_matches_highs():
+    lp = lpgen.transport(1, n_supply=150, n_demand=150, n_arcs=1500)
+    ref = _highs(lp)
+    res, _, _ = oracle.solve(lp, oracle.Options(alpha=1e-4), tol=1e-8, iter_limit=200_000)
+    assert res.status == oracle.pdhg.OPTIMAL
+    assert res.pobj == pytest.approx(ref, rel=1e-6)
+    # strong duality at the returned point
+    assert res.dobj == pytest.approx(ref, rel=1e-6)
