@@ -1,0 +1,202 @@
+/*
+ * lpop.h -- C ABI of the GB300 library for PDHG with online preconditioning
+ * (H. Lu and W. Zhang, "Enhanced PDHG for Linear Programming with Online
+ * Preconditioning", arXiv 2506.17650).
+ *
+ * Problem (Eq. (1) of the paper, generalised to row senses and bounds):
+ *
+ *     min  c^T x   s.t.  A_i x (= | <= | >=) b_i  (i < m),   lb <= x <= ub.
+ *
+ * The library preprocesses the LP (Ruiz equilibration, then Pock-Chambolle or
+ * L2 rescaling, Section 2 and Section 4.2), keeps every vector and both CSR
+ * copies (A and A^T) resident in device memory, and runs the iteration of
+ * Algorithm 1 with the step of Eq. (6): two sparse products fused with the
+ * preconditioned primal/dual updates and projections, the online-gradient
+ * update of the diagonal preconditioners T and Sigma (Eq. (7), every phi
+ * accepted steps, optionally normalised), and KKT / restart reductions.
+ *
+ * Conventions for every function:
+ *  - All pointer arguments are HOST pointers unless stated otherwise.  Input
+ *    arrays are caller-owned and only read during the call (copied to the
+ *    device); output arrays are caller-allocated.
+ *  - The library owns all device memory of a problem and frees it in
+ *    lp_destroy().
+ *  - Every function returns an lp_err code (LP_OK = 0 on success); no C++
+ *    exception crosses the ABI.  On failure lp_last_error() describes it.
+ *  - The solve outcome (optimal, iteration limit, ...) is an lp_status,
+ *    returned through an out-parameter, not as the error code.
+ *  - Infinite bounds are IEEE +-INFINITY.  nnz must be below 2^31.
+ *  - A problem is not thread-safe: calls on one handle must not overlap.
+ */
+#ifndef LPOP_H
+#define LPOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lp_problem lp_problem; /* opaque handle, owned by the library */
+
+/* error codes (function return values) */
+enum {
+  LP_OK = 0,
+  LP_ERR_INVALID_ARG = -1,   /* NULL pointer, bad size or bad option */
+  LP_ERR_INVALID_INPUT = -2, /* NaN/Inf data, index out of range, lb > ub, ... */
+  LP_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  LP_ERR_OOM = -4,           /* device allocation failed */
+  LP_ERR_NOT_SOLVED = -5     /* lp_result() before any lp_solve() */
+};
+
+/* solve outcome (lp_solve status_out, lp_stats.status) */
+enum {
+  LP_STATUS_NONE = 0,
+  LP_OPTIMAL = 1,          /* relative KKT error within the tolerance */
+  LP_ITERATION_LIMIT = 2,  /* iteration limit reached first */
+  LP_TIME_LIMIT = 3,       /* options.time_limit seconds elapsed first */
+  LP_NUMERICAL_ERROR = 4   /* a KKT quantity became NaN or Inf */
+};
+
+/* options.mode */
+enum {
+  LP_MODE_PLAIN = 0, /* vanilla PDHG (Section 4.2): fixed step 0.9/||A~||_2, no restarts */
+  LP_MODE_PDLP = 1   /* Eq. (6): adaptive step size, primal weight, restarts (Section 3.2) */
+};
+
+/* options.scheduler: learning-rate rule of the online update (Section 4.1 names AdaGrad) */
+enum {
+  LP_SCHED_ADAGRAD = 0,      /* per-coordinate AdaGrad */
+  LP_SCHED_ADAGRAD_NORM = 1, /* one AdaGrad accumulator per side */
+  LP_SCHED_CONST = 2         /* constant learning rate */
+};
+
+typedef struct lp_options {
+  int32_t mode;              /* LP_MODE_*; default LP_MODE_PDLP */
+  int32_t scheduler;         /* LP_SCHED_*; default LP_SCHED_ADAGRAD */
+  double alpha;              /* online learning rate; 0 keeps T = Sigma = I (vanilla) */
+  int32_t phi;               /* update period phi (Section 3.2); <= 0 never updates; default 20 */
+  int32_t normalize;         /* normalised online loss (Algorithm 1); default 1 */
+  double precond_floor;      /* projection floor for T and Sigma; default 1e-6 */
+  int32_t ruiz_iters;        /* Ruiz rounds (Section 2); default 10 */
+  double pc_beta;            /* Pock-Chambolle exponent beta in [0, 2] (pdlp mode); default 1 */
+  int32_t check_every;       /* attempts between KKT / restart checks; default 64 */
+  int32_t restart;           /* adaptive restarts in pdlp mode; default 1 */
+  int32_t power_iters;       /* power iterations for ||A~||_2 (plain mode); default 200 */
+  double plain_step_factor;  /* plain mode step = factor / ||A~||_2; default 0.9 */
+  double time_limit;         /* seconds per lp_solve call; <= 0 means none; default 0 */
+  int32_t use_graph;         /* replay one check period as a CUDA graph; default 1 */
+  int32_t kernel_timing;     /* time sampled launches of the hot kernels with CUDA events; default 0 */
+  int32_t device;            /* CUDA device ordinal; -1 = the calling thread's current device */
+  void* stream;              /* cudaStream_t every launch and copy goes to; NULL = default stream */
+  int32_t reserved[8];       /* must be zero */
+} lp_options;
+
+typedef struct lp_stats {
+  double pobj;               /* c^T x of the returned point (user units) */
+  double dobj;               /* dual objective of the returned point */
+  double rel_pres;           /* ||primal residual|| / (1 + ||b||) */
+  double rel_dres;           /* ||dual residual|| / (1 + ||c||) */
+  double rel_gap;            /* |pobj - dobj| / (1 + |pobj| + |dobj|) */
+  int64_t iterations;        /* step attempts since create/reset (accepted or not) */
+  int64_t accepted;          /* accepted steps k */
+  int64_t restarts;
+  double eta;                /* current step size */
+  double omega;              /* current primal weight */
+  double solve_ms;           /* wall time of the last lp_solve call */
+  int32_t status;            /* lp_status of the last lp_solve call */
+  int32_t reserved;
+} lp_stats;
+
+/* Fill *opt with the defaults listed above.  Never fails. */
+void lp_options_default(lp_options* opt);
+
+/*
+ * Create a problem from the CSR form of A (Eq. (1); problem statement of
+ * Section 2) and preprocess it on the device.
+ *   m, n          rows (constraints) and columns (variables), m >= 0, n >= 1
+ *   nnz           number of stored entries, == row_ptr[m], < 2^31
+ *   row_ptr       int64[m+1], non-decreasing, row_ptr[0] == 0
+ *   col_idx       int32[nnz], each in [0, n); any order within a row;
+ *                 repeated (row, col) entries are summed
+ *   val           double[nnz], finite
+ *   b             double[m], finite
+ *   c             double[n], finite
+ *   lb, ub        double[n]; lb < +inf, ub > -inf, lb <= ub; +-INFINITY allowed
+ *   sense         char[m]: 'E' (=), 'L' (<=) or 'G' (>=)
+ *   opt           options (NULL = defaults); opt->stream is kept for all later calls
+ *   out           receives the handle on success, NULL on failure
+ * Errors: LP_ERR_INVALID_ARG, LP_ERR_INVALID_INPUT (data checked on the host
+ * before any device work), LP_ERR_CUDA, LP_ERR_OOM.
+ * The call returns after the preprocessing has finished on the device.
+ */
+int lp_create(int32_t m, int32_t n, int64_t nnz,
+              const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+              const double* b, const double* c,
+              const double* lb, const double* ub, const char* sense,
+              const lp_options* opt, lp_problem** out);
+
+/*
+ * Run the iteration (Algorithm 1 with Eq. (6)) until the relative KKT error
+ * (Section 4.1 tolerance) is at most rel_kkt_tol at a check, or until
+ * iter_limit step attempts have been made since create/reset (the limit is
+ * cumulative, so a second call continues), or until options.time_limit.
+ * A check runs before the first attempt and after every check_every-th
+ * attempt.  *status_out (may be NULL) receives an lp_status.
+ * Errors: LP_ERR_INVALID_ARG (NULL handle, tol < 0), LP_ERR_CUDA.
+ */
+int lp_solve(lp_problem* p, double rel_kkt_tol, int64_t iter_limit, int32_t* status_out);
+
+/*
+ * Copy the current point, in user units and the caller's row/column order,
+ * to x (double[n], may be NULL) and y (double[m], may be NULL; the paper's
+ * lambda), and fill *st (may be NULL) with the KKT statistics of the last
+ * check.  Errors: LP_ERR_INVALID_ARG, LP_ERR_NOT_SOLVED, LP_ERR_CUDA.
+ */
+int lp_result(lp_problem* p, double* x, double* y, lp_stats* st);
+
+/*
+ * Debug / parity access to the iterate in the PREPROCESSED (scaled) space, in
+ * the caller's row/column order: x~ (double[n]), y~ (double[m]), T (double[n]),
+ * Sigma (double[m]); any may be NULL.  A pending preconditioner update is
+ * applied first.  scal (double[8], may be NULL) receives
+ * {eta, omega, k, attempts, wsum, restarts, last_eta_max, last_accept}.
+ * Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
+ */
+int lp_get_iterate(lp_problem* p, double* x, double* y, double* T, double* Sigma, double* scal);
+
+/*
+ * Scaled-space vectors of the preprocessing, caller's order: dr (double[m]),
+ * dc (double[n]) with A~ = diag(dr) A diag(dc), and scal (double[4], may be
+ * NULL) = {eta_0, omega_0, ||A~||_2 estimate (plain mode, else 0), max|A~_ij|}.
+ * Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
+ */
+int lp_get_scaling(lp_problem* p, double* dr, double* dc, double* scal);
+
+/*
+ * Return the problem to its initial state (x_0 = proj(0), y_0 = 0, T = Sigma = I,
+ * eta_0, omega_0, counters zero) without redoing the preprocessing.
+ * Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
+ */
+int lp_reset(lp_problem* p);
+
+/*
+ * Kernel timing (options.kernel_timing = 1): accumulated CUDA-event time in
+ * milliseconds and sample counts of the sampled launches, for up to n_kernels
+ * kernels in the order {primal step, dual step}.  launches (may be NULL)
+ * receives the number of kernel launches issued since create/reset.
+ * Errors: LP_ERR_INVALID_ARG.
+ */
+int lp_kernel_times(lp_problem* p, double* ms, int64_t* samples, int32_t n_kernels, int64_t* launches);
+
+/* Free all device and host memory of the problem.  NULL is ignored. */
+void lp_destroy(lp_problem* p);
+
+/* Last error message of p, or of the calling thread when p is NULL. */
+const char* lp_last_error(const lp_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPOP_H */

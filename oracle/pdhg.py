@@ -129,7 +129,7 @@ class State:
     K_prev: float = math.inf
     last_restart_attempt: int = 0
     restarts: int = 0
-    checked0: bool = False
+    checked0: bool = False  # the check before the first attempt has run
     status: int | None = None
     stats: dict = field(default_factory=dict)
 
@@ -171,8 +171,11 @@ def ruiz_equilibrate(A, iters):
     dc = np.ones(n)
     for _ in range(iters):
         absA = abs(A)
-        r = np.asarray(absA.max(axis=1).todense()).ravel()
-        c = np.asarray(absA.max(axis=0).todense()).ravel()
+        if A.nnz:
+            r = np.asarray(absA.max(axis=1).todense()).ravel()
+            c = np.asarray(absA.max(axis=0).todense()).ravel()
+        else:  # no entries (e.g. m = 0): every factor stays 1
+            r, c = np.zeros(m), np.zeros(n)
         r[r == 0] = 1.0
         c[c == 0] = 1.0
         fr = 1.0 / np.sqrt(r)
@@ -506,12 +509,12 @@ def check(P: Scaled, S: State, opts: Options, tol: float, eval_only: bool = Fals
             return
     if opts.mode != "pdlp":
         return
-    if not S.checked0:
+    if S.x_last is None:
+        # first check that does not terminate: the current point is the first restart reference
         S.x_last, S.y_last = S.x.copy(), S.y.copy()
         S.K_last_parts = cur["parts"]
         S.K_prev = _kw(cur["parts"], S.omega)
         S.last_restart_attempt = S.attempts
-        S.checked0 = True
         return
     if not opts.restart:
         return

@@ -1,0 +1,283 @@
+"""Python binding of liblpop.so: PDHG with online preconditioning for LP on GB300.
+
+Argument marshalling only.  Every step of the method runs in the library's
+CUDA kernels; there is no Python or CPU fallback, and every function raises
+if the shared library has not been built (``python -m
+paper_2506_17650_gb300.build``).  The function names are those of the C ABI
+in ``include/lpop.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblpop.so")
+
+LP_OK = 0
+LP_ERR_INVALID_ARG = -1
+LP_ERR_INVALID_INPUT = -2
+LP_ERR_CUDA = -3
+LP_ERR_OOM = -4
+LP_ERR_NOT_SOLVED = -5
+
+LP_STATUS_NONE = 0
+LP_OPTIMAL = 1
+LP_ITERATION_LIMIT = 2
+LP_TIME_LIMIT = 3
+LP_NUMERICAL_ERROR = 4
+
+LP_MODE_PLAIN = 0
+LP_MODE_PDLP = 1
+
+LP_SCHED_ADAGRAD = 0
+LP_SCHED_ADAGRAD_NORM = 1
+LP_SCHED_CONST = 2
+
+
+class LpOptions(ctypes.Structure):
+    _fields_ = [
+        ("mode", c_int32),
+        ("scheduler", c_int32),
+        ("alpha", c_double),
+        ("phi", c_int32),
+        ("normalize", c_int32),
+        ("precond_floor", c_double),
+        ("ruiz_iters", c_int32),
+        ("pc_beta", c_double),
+        ("check_every", c_int32),
+        ("restart", c_int32),
+        ("power_iters", c_int32),
+        ("plain_step_factor", c_double),
+        ("time_limit", c_double),
+        ("use_graph", c_int32),
+        ("kernel_timing", c_int32),
+        ("device", c_int32),
+        ("stream", c_void_p),
+        ("reserved", c_int32 * 8),
+    ]
+
+
+class LpStats(ctypes.Structure):
+    _fields_ = [
+        ("pobj", c_double),
+        ("dobj", c_double),
+        ("rel_pres", c_double),
+        ("rel_dres", c_double),
+        ("rel_gap", c_double),
+        ("iterations", c_int64),
+        ("accepted", c_int64),
+        ("restarts", c_int64),
+        ("eta", c_double),
+        ("omega", c_double),
+        ("solve_ms", c_double),
+        ("status", c_int32),
+        ("reserved", c_int32),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+class LpError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"lpop error {code}: {message}")
+        self.code = code
+
+
+_lib = None
+_DP = POINTER(c_double)
+
+
+def load_library(path: str | None = None):
+    """Load liblpop.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{path} is missing; build it with `python -m paper_2506_17650_gb300.build` "
+            "(the solver has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    lib.lp_options_default.argtypes = [POINTER(LpOptions)]
+    lib.lp_options_default.restype = None
+    lib.lp_create.argtypes = [c_int32, c_int32, c_int64, POINTER(c_int64), POINTER(c_int32), _DP, _DP, _DP, _DP,
+                              _DP, c_char_p, POINTER(LpOptions), POINTER(c_void_p)]
+    lib.lp_create.restype = c_int32
+    lib.lp_solve.argtypes = [c_void_p, c_double, c_int64, POINTER(c_int32)]
+    lib.lp_solve.restype = c_int32
+    lib.lp_result.argtypes = [c_void_p, _DP, _DP, POINTER(LpStats)]
+    lib.lp_result.restype = c_int32
+    lib.lp_get_iterate.argtypes = [c_void_p, _DP, _DP, _DP, _DP, _DP]
+    lib.lp_get_iterate.restype = c_int32
+    lib.lp_get_scaling.argtypes = [c_void_p, _DP, _DP, _DP]
+    lib.lp_get_scaling.restype = c_int32
+    lib.lp_reset.argtypes = [c_void_p]
+    lib.lp_reset.restype = c_int32
+    lib.lp_kernel_times.argtypes = [c_void_p, _DP, POINTER(c_int64), c_int32, POINTER(c_int64)]
+    lib.lp_kernel_times.restype = c_int32
+    lib.lp_destroy.argtypes = [c_void_p]
+    lib.lp_destroy.restype = None
+    lib.lp_last_error.argtypes = [c_void_p]
+    lib.lp_last_error.restype = c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc, handle=None):
+    if rc != LP_OK:
+        msg = load_library().lp_last_error(handle)
+        raise LpError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(POINTER(ctype)) if a is not None else None
+
+
+def _out(n):
+    return np.empty(n, dtype=np.float64)
+
+
+def lp_options_default(**overrides) -> LpOptions:
+    """Default options, with keyword overrides (e.g. ``alpha=1e-3, phi=20``)."""
+    o = LpOptions()
+    load_library().lp_options_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "stream" and v is not None:
+            v = int(v)
+        setattr(o, k, v)
+    return o
+
+
+def lp_create(m, n, row_ptr, col_idx, val, b, c, lb, ub, sense, opts: LpOptions | None = None):
+    """Create a problem from host arrays (CSR of A, b, c, bounds, senses 'E'/'L'/'G')."""
+    lib = load_library()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    lb = np.ascontiguousarray(lb, dtype=np.float64)
+    ub = np.ascontiguousarray(ub, dtype=np.float64)
+    if isinstance(sense, str):
+        sense = sense.encode()
+    sense = np.ascontiguousarray(np.frombuffer(bytes(sense), dtype=np.uint8) if isinstance(sense, bytes) else sense,
+                                 dtype=np.uint8)
+    if row_ptr.size != m + 1 or b.size != m or sense.size != m or c.size != n or lb.size != n or ub.size != n:
+        raise LpError(LP_ERR_INVALID_ARG, "array sizes do not match m and n")
+    handle = c_void_p()
+    rc = lib.lp_create(int(m), int(n), int(row_ptr[-1]) if row_ptr.size else 0, _ptr(row_ptr, c_int64),
+                       _ptr(col_idx, c_int32), _ptr(val, c_double), _ptr(b, c_double), _ptr(c, c_double),
+                       _ptr(lb, c_double), _ptr(ub, c_double), sense.ctypes.data_as(c_char_p),
+                       ctypes.byref(opts) if opts is not None else None, ctypes.byref(handle))
+    _check(rc)
+    return handle
+
+
+def lp_solve(handle, rel_kkt_tol=1e-4, iter_limit=1_000_000) -> int:
+    """Run until the relative KKT tolerance or the (cumulative) iteration limit; returns an LP_* status."""
+    st = c_int32(0)
+    _check(load_library().lp_solve(handle, float(rel_kkt_tol), int(iter_limit), ctypes.byref(st)), handle)
+    return st.value
+
+
+def lp_result(handle, m, n, want_x=True, want_y=True):
+    """(x, y, stats) in user units and the caller's order."""
+    x = _out(n) if want_x else None
+    y = _out(m) if want_y else None
+    st = LpStats()
+    _check(load_library().lp_result(handle, _ptr(x, c_double), _ptr(y, c_double), ctypes.byref(st)), handle)
+    return x, y, st.as_dict()
+
+
+def lp_get_iterate(handle, m, n):
+    """Scaled-space iterate: dict(x, y, T, Sigma, eta, omega, k, attempts, wsum, restarts, eta_max, accepted)."""
+    x, y, T, S, scal = _out(n), _out(m), _out(n), _out(m), _out(8)
+    _check(load_library().lp_get_iterate(handle, _ptr(x, c_double), _ptr(y, c_double), _ptr(T, c_double),
+                                         _ptr(S, c_double), _ptr(scal, c_double)), handle)
+    return dict(x=x, y=y, T=T, Sigma=S, eta=scal[0], omega=scal[1], k=int(scal[2]), attempts=int(scal[3]),
+                wsum=scal[4], restarts=int(scal[5]), eta_max=scal[6], accepted=bool(scal[7]))
+
+
+def lp_get_scaling(handle, m, n):
+    """(dr, dc, dict(eta0, omega0, norm_est, amax)) with A~ = diag(dr) A diag(dc)."""
+    dr, dc, scal = _out(m), _out(n), _out(4)
+    _check(load_library().lp_get_scaling(handle, _ptr(dr, c_double), _ptr(dc, c_double), _ptr(scal, c_double)),
+           handle)
+    return dr, dc, dict(eta0=scal[0], omega0=scal[1], norm_est=scal[2], amax=scal[3])
+
+
+def lp_reset(handle):
+    _check(load_library().lp_reset(handle), handle)
+
+
+def lp_kernel_times(handle):
+    """(ms[2], samples[2], launches): event-timed primal / dual step kernels and the launch count."""
+    ms = _out(2)
+    ns = np.zeros(2, dtype=np.int64)
+    launches = c_int64(0)
+    _check(load_library().lp_kernel_times(handle, _ptr(ms, c_double), _ptr(ns, c_int64), 2, ctypes.byref(launches)),
+           handle)
+    return ms, ns, launches.value
+
+
+def lp_destroy(handle):
+    if handle:
+        load_library().lp_destroy(handle)
+
+
+def lp_last_error(handle=None) -> str:
+    msg = load_library().lp_last_error(handle)
+    return msg.decode() if msg else ""
+
+
+class Problem:
+    """Owning wrapper: ``with Problem(lp, alpha=1e-3) as p: p.solve(1e-4)``.
+
+    ``lp`` is any object with the attributes m, n, row_ptr, col_idx, val, b,
+    c, lb, ub, sense (the caller's host arrays)."""
+
+    def __init__(self, lp, **options):
+        self.m, self.n = int(lp.m), int(lp.n)
+        self.options = lp_options_default(**options)
+        self.handle = lp_create(self.m, self.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, lp.lb, lp.ub,
+                                lp.sense, self.options)
+
+    def solve(self, rel_kkt_tol=1e-4, iter_limit=1_000_000):
+        return lp_solve(self.handle, rel_kkt_tol, iter_limit)
+
+    def result(self, want_x=True, want_y=True):
+        return lp_result(self.handle, self.m, self.n, want_x, want_y)
+
+    def iterate(self):
+        return lp_get_iterate(self.handle, self.m, self.n)
+
+    def scaling(self):
+        return lp_get_scaling(self.handle, self.m, self.n)
+
+    def reset(self):
+        lp_reset(self.handle)
+
+    def kernel_times(self):
+        return lp_kernel_times(self.handle)
+
+    def close(self):
+        if self.handle:
+            lp_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,686 @@
+// C ABI of the library (declared in include/lpop.h).
+//
+// lp_create validates on the host, builds the bin-ordered CSR copies of A and
+// A^T, uploads them and runs the preprocessing kernels.  lp_solve drives the
+// device-resident iteration: one check period (check_every step attempts and
+// the KKT check) is captured once as a CUDA graph and replayed; the host only
+// reads one status word per period.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lpop.h"
+#include "common.cuh"
+#include "host_layout.hpp"
+
+using namespace lpop;
+
+namespace lpop {
+void launch_mul_into(double* out, const double* a, const double* f, int n, cudaStream_t s);
+int row_kernel_blocks_per_sm();
+}  // namespace lpop
+
+static thread_local std::string g_last_error;
+
+struct lp_problem {
+  lp_options opt{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Dev d{};
+  Params prm{};
+  std::vector<int> prow, pcol;
+  double eta0 = 1.0, omega0 = 1.0, norm_est = 0.0, amax = 0.0;
+  long long nnz = 0;
+  bool initial_check_done = false;
+  bool solved_once = false;
+  int last_status = LP_STATUS_NONE;
+  double last_solve_ms = 0.0;
+  long long host_attempts = 0;
+  long long launches = 0;
+  std::string err;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<cudaEvent_t> events;  // 3 per timed sample: before primal, between, after dual
+  int samples = 0;
+  double kt_ms[2] = {0.0, 0.0};
+  long long kt_n[2] = {0, 0};
+  int* h_status = nullptr;  // pinned
+  double* h_scratch = nullptr;  // pinned, 8 doubles
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int set_err(lp_problem* p, int code, const std::string& msg) {
+  if (p) p->err = msg;
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return set_err(p, e_ == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,           \
+                     std::string(#call) + " failed: " + cudaGetErrorString(e_));              \
+  } while (0)
+
+template <class T>
+int dalloc(lp_problem* p, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+  if (e != cudaSuccess) {
+    return set_err(p, e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
+                   std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes failed: " +
+                       cudaGetErrorString(e));
+  }
+  p->allocs.push_back(v);
+  *ptr = static_cast<T*>(v);
+  return LP_OK;
+}
+
+#define TRY(expr)            \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != LP_OK) return rc_; \
+  } while (0)
+
+int check_options(const lp_options& o, std::string& msg) {
+  if (o.mode != LP_MODE_PLAIN && o.mode != LP_MODE_PDLP) return msg = "mode must be LP_MODE_PLAIN or LP_MODE_PDLP", 1;
+  if (o.scheduler < 0 || o.scheduler > 2) return msg = "unknown scheduler", 1;
+  if (!(o.alpha >= 0.0) || !std::isfinite(o.alpha)) return msg = "alpha must be finite and >= 0", 1;
+  if (!(o.precond_floor > 0.0) || !std::isfinite(o.precond_floor)) return msg = "precond_floor must be > 0", 1;
+  if (o.ruiz_iters < 0 || o.ruiz_iters > 1000) return msg = "ruiz_iters must be in [0, 1000]", 1;
+  if (!(o.pc_beta >= 0.0 && o.pc_beta <= 2.0)) return msg = "pc_beta must be in [0, 2]", 1;
+  if (o.check_every < 1) return msg = "check_every must be >= 1", 1;
+  if (o.power_iters < 1) return msg = "power_iters must be >= 1", 1;
+  if (!(o.plain_step_factor > 0.0)) return msg = "plain_step_factor must be > 0", 1;
+  for (int i = 0; i < 8; ++i)
+    if (o.reserved[i] != 0) return msg = "reserved option fields must be zero", 1;
+  return 0;
+}
+
+int select_device(lp_problem* p) {
+  CK(cudaSetDevice(p->device));
+  return LP_OK;
+}
+
+int read_status(lp_problem* p, int* status) {
+  CK(cudaMemcpyAsync(p->h_status, &p->d.st->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  *status = *p->h_status;
+  return LP_OK;
+}
+
+int init_state(lp_problem* p) {
+  DevState s0;
+  std::memset(&s0, 0, sizeof(s0));
+  s0.cur = 0;
+  s0.eta = p->eta0;
+  s0.omega = p->omega0;
+  s0.tol = 1e-4;
+  s0.k_prev = INFINITY;
+  CK(cudaMemcpyAsync(p->d.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, p->stream));
+  launch_init_vectors(p->d, p->stream);
+  launch_spmv_binned(p->d.A, p->d.binsA, p->d.gridA, p->d.x[0], p->d.ax[0], p->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(p->stream));
+  p->initial_check_done = false;
+  p->solved_once = false;
+  p->host_attempts = 0;
+  p->launches = 0;
+  p->kt_ms[0] = p->kt_ms[1] = 0.0;
+  p->kt_n[0] = p->kt_n[1] = 0;
+  p->last_status = LP_STATUS_NONE;
+  return LP_OK;
+}
+
+double read_scalar(lp_problem* p, const double* dptr, int* rc) {
+  cudaError_t e = cudaMemcpyAsync(p->h_scratch, dptr, sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) {
+    *rc = set_err(p, LP_ERR_CUDA, std::string("reading a device scalar failed: ") + cudaGetErrorString(e));
+    return 0.0;
+  }
+  return p->h_scratch[0];
+}
+
+int preprocess(lp_problem* p) {
+  Dev& d = p->d;
+  cudaStream_t s = p->stream;
+  const int m = d.m, n = d.n;
+  double* fr = d.work;           // [m]
+  double* fc = d.work + m;       // [n]
+  double* red = d.work + m + n;  // reduction scratch [1 + 1024]
+  launch_fill(d.dr, 1.0, m, s);
+  launch_fill(d.dc, 1.0, n, s);
+  auto apply = [&]() {
+    launch_factor_from_norm(fr, m, s);
+    launch_factor_from_norm(fc, n, s);
+    launch_scale_values(d.A_rp, d.A_ci, d.A_v, m, fr, fc, 1, s);
+    launch_scale_values(d.At_rp, d.At_ci, d.At_v, n, fr, fc, 0, s);
+    launch_mul_inplace(d.dr, fr, m, s);
+    launch_mul_inplace(d.dc, fc, n, s);
+  };
+  for (int r = 0; r < p->opt.ruiz_iters; ++r) {
+    launch_row_absmax(d.A, m, fr, s);
+    launch_row_absmax(d.At, n, fc, s);
+    apply();
+  }
+  if (p->opt.mode == LP_MODE_PDLP) {
+    launch_row_powsum(d.A, m, p->opt.pc_beta, 0, fr, s);
+    launch_row_powsum(d.At, n, 2.0 - p->opt.pc_beta, 0, fc, s);
+  } else {
+    launch_row_powsum(d.A, m, 2.0, 1, fr, s);
+    launch_row_powsum(d.At, n, 2.0, 1, fc, s);
+  }
+  apply();
+  CK(cudaGetLastError());
+  int rc = LP_OK;
+  // norms of the caller's b and c (still unscaled), then rescale the vectors
+  launch_norm2(d.b, m, red, s);
+  p->prm.b_norm = m > 0 ? read_scalar(p, red, &rc) : 0.0;
+  TRY(rc);
+  launch_norm2(d.c, n, red, s);
+  p->prm.c_norm = read_scalar(p, red, &rc);
+  TRY(rc);
+  launch_scale_problem_vectors(d, s);
+  launch_norm2(d.b, m, red, s);
+  const double bn = m > 0 ? read_scalar(p, red, &rc) : 0.0;
+  TRY(rc);
+  launch_norm2(d.c, n, red, s);
+  const double cn = read_scalar(p, red, &rc);
+  TRY(rc);
+  p->omega0 = (bn > 0.0 && cn > 0.0) ? cn / bn : 1.0;
+  if (p->nnz > 0) {
+    launch_absmax(d.A_v, p->nnz, red, s);
+    p->amax = read_scalar(p, red, &rc);
+    TRY(rc);
+  } else {
+    p->amax = 0.0;
+  }
+  if (p->opt.mode == LP_MODE_PDLP) {
+    p->eta0 = p->amax > 0.0 ? 1.0 / p->amax : 1.0;
+  } else {
+    // ||A~||_2 by power iteration on A~^T A~ from the all-ones direction
+    double* v = d.q;       // [n]
+    double* t = d.ax_avg;  // [m]
+    double* w = fc;        // [n]
+    p->norm_est = 0.0;
+    if (p->nnz > 0) {
+      launch_fill(v, 1.0 / std::sqrt((double)n), n, s);
+      for (int it = 0; it < p->opt.power_iters; ++it) {
+        launch_spmv_binned(d.A, d.binsA, d.gridA, v, t, s);
+        launch_spmv_binned(d.At, d.binsAt, d.gridAt, t, w, s);
+        launch_norm2(w, n, red, s);
+        launch_scale_by_inv(w, n, red, s);
+        CK(cudaMemcpyAsync(v, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      }
+      const double nw = read_scalar(p, red, &rc);
+      TRY(rc);
+      p->norm_est = std::sqrt(nw);
+    }
+    p->eta0 = p->norm_est > 0.0 ? p->opt.plain_step_factor / p->norm_est : 1.0;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return LP_OK;
+}
+
+int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* c, const double* lb,
+           const double* ub, const char* sense) {
+  Dev& d = p->d;
+  const int m = lay.m, n = lay.n;
+  const long long nz = lay.nnz;
+  d.m = m;
+  d.n = n;
+  TRY(dalloc(p, &d.A_rp, m + 1));
+  TRY(dalloc(p, &d.A_ci, nz));
+  TRY(dalloc(p, &d.A_v, nz));
+  TRY(dalloc(p, &d.At_rp, n + 1));
+  TRY(dalloc(p, &d.At_ci, nz));
+  TRY(dalloc(p, &d.At_v, nz));
+  double** vecs_m[] = {&d.b, &d.dr, &d.y[0], &d.y[1], &d.ax[0], &d.ax[1], &d.ybar[0], &d.ybar[1],
+                       &d.S, &d.GS, &d.p, &d.y_last, &d.ax_avg};
+  for (double** v : vecs_m) TRY(dalloc(p, v, m));
+  double** vecs_n[] = {&d.c, &d.l, &d.u, &d.dc, &d.x[0], &d.x[1], &d.xbar[0], &d.xbar[1],
+                       &d.T, &d.GT, &d.q, &d.x_last};
+  for (double** v : vecs_n) TRY(dalloc(p, v, n));
+  TRY(dalloc(p, &d.sense, m));
+  TRY(dalloc(p, &d.work, (size_t)m + n + 2048));
+  TRY(dalloc(p, &d.st, 1));
+
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+  int per_sm = row_kernel_blocks_per_sm();
+  if (per_sm < 1) per_sm = 1;
+  d.max_grid = sms * per_sm;
+  d.binsA = lay.binsA;
+  d.binsAt = lay.binsAt;
+  d.gridA = d.binsA.nunits < d.max_grid ? d.binsA.nunits : d.max_grid;
+  d.gridAt = d.binsAt.nunits < d.max_grid ? d.binsAt.nunits : d.max_grid;
+  if (d.gridA < 1) d.gridA = 1;
+  if (d.gridAt < 1) d.gridAt = 1;
+  const int maxg = d.gridA > d.gridAt ? d.gridA : d.gridAt;
+  TRY(dalloc(p, &d.partials, (size_t)maxg * kMaxPartials));
+  TRY(dalloc(p, &d.partials2, (size_t)maxg * kMaxPartials));
+  d.A = Csr{d.A_rp, d.A_ci, d.A_v};
+  d.At = Csr{d.At_rp, d.At_ci, d.At_v};
+
+  cudaStream_t s = p->stream;
+  CK(cudaMemcpyAsync(d.A_rp, lay.A_rp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d.At_rp, lay.At_rp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+  if (nz > 0) {
+    CK(cudaMemcpyAsync(d.A_ci, lay.A_ci.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d.A_v, lay.A_v.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d.At_ci, lay.At_ci.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d.At_v, lay.At_v.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, s));
+  }
+  // vectors in bin order
+  std::vector<double> tm(m), tn(n);
+  std::vector<uint8_t> ts(m);
+  for (int i = 0; i < m; ++i) tm[i] = b[lay.prow[i]];
+  if (m > 0) CK(cudaMemcpyAsync(d.b, tm.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  for (int i = 0; i < m; ++i) {
+    const char c0 = sense[lay.prow[i]];
+    ts[i] = c0 == 'E' ? kEq : (c0 == 'L' ? kLe : kGe);
+  }
+  if (m > 0) CK(cudaMemcpyAsync(d.sense, ts.data(), m, cudaMemcpyHostToDevice, s));
+  for (int j = 0; j < n; ++j) tn[j] = c[lay.pcol[j]];
+  CK(cudaMemcpyAsync(d.c, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // tn is reused below
+  for (int j = 0; j < n; ++j) tn[j] = lb[lay.pcol[j]];
+  CK(cudaMemcpyAsync(d.l, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  for (int j = 0; j < n; ++j) tn[j] = ub[lay.pcol[j]];
+  CK(cudaMemcpyAsync(d.u, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return LP_OK;
+}
+
+int create_events(lp_problem* p) {
+  if (!p->opt.kernel_timing) return LP_OK;
+  p->samples = (p->opt.check_every + 7) / 8;
+  p->events.resize(3 * p->samples, nullptr);
+  for (auto& e : p->events) CK(cudaEventCreate(&e));
+  return LP_OK;
+}
+
+bool sampled(const lp_problem* p, int a) { return p->opt.kernel_timing && (a % 8) == 0; }
+
+int capture_graph(lp_problem* p) {
+  if (p->gexec) return LP_OK;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+  const int ce = p->opt.check_every;
+  for (int a = 0; a < ce; ++a) {
+    const bool tm = sampled(p, a);
+    const int sidx = a / 8;
+    if (tm) cudaEventRecordWithFlags(p->events[3 * sidx], p->stream, cudaEventRecordExternal);
+    launch_primal(p->d, p->prm, p->stream);
+    if (tm) cudaEventRecordWithFlags(p->events[3 * sidx + 1], p->stream, cudaEventRecordExternal);
+    launch_dual(p->d, p->prm, p->stream);
+    if (tm) cudaEventRecordWithFlags(p->events[3 * sidx + 2], p->stream, cudaEventRecordExternal);
+  }
+  launch_check(p->d, p->prm, 0, p->stream);
+  cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+  if (e != cudaSuccess) return set_err(p, LP_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&p->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    p->gexec = nullptr;
+    return set_err(p, LP_ERR_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+  }
+  return LP_OK;
+}
+
+int collect_times(lp_problem* p) {
+  if (!p->opt.kernel_timing) return LP_OK;
+  for (int sidx = 0; sidx < p->samples; ++sidx) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, p->events[3 * sidx], p->events[3 * sidx + 1]));
+    CK(cudaEventElapsedTime(&b, p->events[3 * sidx + 1], p->events[3 * sidx + 2]));
+    p->kt_ms[0] += a;
+    p->kt_ms[1] += b;
+    p->kt_n[0] += 1;
+    p->kt_n[1] += 1;
+  }
+  return LP_OK;
+}
+
+int download_vec(lp_problem* p, const double* dsrc, const double* dscale, int len, const std::vector<int>& perm,
+                 double* out) {
+  if (!out || len == 0) return LP_OK;
+  double* tmp = p->d.work;  // [m + n + 2048] >= len
+  if (dscale) {
+    launch_mul_into(tmp, dsrc, dscale, len, p->stream);
+    CK(cudaGetLastError());
+    dsrc = tmp;
+  }
+  std::vector<double> h(len);
+  CK(cudaMemcpyAsync(h.data(), dsrc, sizeof(double) * len, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  for (int i = 0; i < len; ++i) out[perm[i]] = h[i];
+  return LP_OK;
+}
+
+void release(lp_problem* p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  for (auto e : p->events)
+    if (e) cudaEventDestroy(e);
+  for (void* v : p->allocs) cudaFree(v);
+  if (p->h_status) cudaFreeHost(p->h_status);
+  if (p->h_scratch) cudaFreeHost(p->h_scratch);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                const double* val, const double* b, const double* c, const double* lb, const double* ub,
+                const char* sense, const lp_options* opt, lp_problem** out) {
+  lp_problem* p = nullptr;
+  if (!out) return set_err(nullptr, LP_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  lp_options o;
+  if (opt) o = *opt;
+  else lp_options_default(&o);
+  std::string msg;
+  if (check_options(o, msg)) return set_err(nullptr, LP_ERR_INVALID_ARG, msg);
+  if (m < 0 || n < 1) return set_err(nullptr, LP_ERR_INVALID_ARG, "need m >= 0 and n >= 1");
+  if ((m > 0 && (!b || !sense)) || !c || !lb || !ub)
+    return set_err(nullptr, LP_ERR_INVALID_ARG, "b, c, lb, ub and sense must not be NULL");
+  for (int i = 0; i < m; ++i) {
+    if (!std::isfinite(b[i])) return set_err(nullptr, LP_ERR_INVALID_INPUT, "b[" + std::to_string(i) + "] is not finite");
+    if (sense[i] != 'E' && sense[i] != 'L' && sense[i] != 'G')
+      return set_err(nullptr, LP_ERR_INVALID_INPUT, "sense[" + std::to_string(i) + "] must be 'E', 'L' or 'G'");
+  }
+  for (int j = 0; j < n; ++j) {
+    if (!std::isfinite(c[j])) return set_err(nullptr, LP_ERR_INVALID_INPUT, "c[" + std::to_string(j) + "] is not finite");
+    if (std::isnan(lb[j]) || std::isnan(ub[j]) || lb[j] == INFINITY || ub[j] == -INFINITY || lb[j] > ub[j])
+      return set_err(nullptr, LP_ERR_INVALID_INPUT,
+                     "bounds of variable " + std::to_string(j) + " are invalid (need lb <= ub, lb < inf, ub > -inf)");
+  }
+  HostLayout lay;
+  int rc = build_layout(m, n, nnz, row_ptr, col_idx, val, lay, msg);
+  if (rc != LP_OK) return set_err(nullptr, rc, msg);
+
+  p = new lp_problem();
+  p->opt = o;
+  p->nnz = lay.nnz;
+  auto fail = [&](int code) {
+    g_last_error = p->err;
+    release(p);
+    return code;
+  };
+  cudaError_t e = cudaSuccess;
+  if (o.device >= 0) e = cudaSetDevice(o.device);
+  if (e == cudaSuccess) e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    set_err(p, LP_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+    return fail(LP_ERR_CUDA);
+  }
+  if (o.stream) {
+    p->stream = static_cast<cudaStream_t>(o.stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      set_err(p, LP_ERR_CUDA, std::string("stream creation failed: ") + cudaGetErrorString(e));
+      return fail(LP_ERR_CUDA);
+    }
+    p->own_stream = true;
+  }
+  if (cudaMallocHost(&p->h_status, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&p->h_scratch, 8 * sizeof(double)) != cudaSuccess) {
+    set_err(p, LP_ERR_OOM, "pinned host allocation failed");
+    return fail(LP_ERR_OOM);
+  }
+  p->prow = lay.prow;
+  p->pcol = lay.pcol;
+  p->prm.m = m;
+  p->prm.n = n;
+  p->prm.mode = o.mode;
+  p->prm.sched = o.scheduler;
+  p->prm.phi = o.phi;
+  p->prm.normalize = o.normalize ? 1 : 0;
+  p->prm.restart = o.restart ? 1 : 0;
+  p->prm.check_every = o.check_every;
+  p->prm.alpha = o.alpha;
+  p->prm.floor = o.precond_floor;
+  if ((rc = upload(p, lay, b, c, lb, ub, sense)) != LP_OK) return fail(rc);
+  if ((rc = preprocess(p)) != LP_OK) return fail(rc);
+  if ((rc = create_events(p)) != LP_OK) return fail(rc);
+  if ((rc = init_state(p)) != LP_OK) return fail(rc);
+  *out = p;
+  return LP_OK;
+}
+
+int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_out) {
+  TRY(select_device(p));
+  const auto t0 = std::chrono::steady_clock::now();
+  const int ce = p->opt.check_every;
+  // tolerance and a cleared status for this call
+  p->h_scratch[0] = tol;
+  CK(cudaMemcpyAsync(&p->d.st->tol, p->h_scratch, sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  *p->h_status = 0;
+  CK(cudaMemcpyAsync(&p->d.st->status, p->h_status, sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  int status = 0;
+  if (!p->initial_check_done) {
+    launch_check(p->d, p->prm, 0, p->stream);
+    CK(cudaGetLastError());
+    p->launches += check_kernel_count();
+    p->initial_check_done = true;
+    TRY(read_status(p, &status));
+  }
+  int out_status = LP_STATUS_NONE;
+  while (status == 0 && p->host_attempts < iter_limit) {
+    const long long to_boundary = ce - p->host_attempts % ce;
+    const long long remaining = iter_limit - p->host_attempts;
+    if (p->opt.use_graph && to_boundary == ce && remaining >= ce) {
+      TRY(capture_graph(p));
+      CK(cudaGraphLaunch(p->gexec, p->stream));
+      p->launches += 2LL * ce + check_kernel_count();
+      p->host_attempts += ce;
+      TRY(read_status(p, &status));
+      TRY(collect_times(p));
+    } else {
+      const long long nrun = to_boundary < remaining ? to_boundary : remaining;
+      for (long long a = 0; a < nrun; ++a) {
+        launch_primal(p->d, p->prm, p->stream);
+        launch_dual(p->d, p->prm, p->stream);
+      }
+      CK(cudaGetLastError());
+      p->launches += 2 * nrun;
+      p->host_attempts += nrun;
+      if (p->host_attempts % ce == 0) {
+        launch_check(p->d, p->prm, 0, p->stream);
+        CK(cudaGetLastError());
+        p->launches += check_kernel_count();
+      }
+      TRY(read_status(p, &status));
+    }
+    if (p->opt.time_limit > 0.0) {
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (status == 0 && el > p->opt.time_limit) {
+        out_status = LP_TIME_LIMIT;
+        break;
+      }
+    }
+  }
+  if (status == 1) out_status = LP_OPTIMAL;
+  else if (status == 4) out_status = LP_NUMERICAL_ERROR;
+  else if (out_status == LP_STATUS_NONE) out_status = LP_ITERATION_LIMIT;
+  if ((out_status == LP_ITERATION_LIMIT || out_status == LP_TIME_LIMIT) && p->host_attempts % ce != 0) {
+    launch_check(p->d, p->prm, 1, p->stream);
+    CK(cudaGetLastError());
+    p->launches += check_kernel_count();
+  }
+  CK(cudaStreamSynchronize(p->stream));
+  p->last_status = out_status;
+  p->solved_once = true;
+  p->last_solve_ms = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (status_out) *status_out = out_status;
+  return LP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lp_options_default(lp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->mode = LP_MODE_PDLP;
+  o->scheduler = LP_SCHED_ADAGRAD;
+  o->alpha = 0.0;
+  o->phi = 20;
+  o->normalize = 1;
+  o->precond_floor = 1e-6;
+  o->ruiz_iters = 10;
+  o->pc_beta = 1.0;
+  o->check_every = 64;
+  o->restart = 1;
+  o->power_iters = 200;
+  o->plain_step_factor = 0.9;
+  o->time_limit = 0.0;
+  o->use_graph = 1;
+  o->kernel_timing = 0;
+  o->device = -1;
+  o->stream = nullptr;
+}
+
+const char* lp_last_error(const lp_problem* p) {
+  if (p) return p->err.c_str();
+  return g_last_error.c_str();
+}
+
+int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+              const double* b, const double* c, const double* lb, const double* ub, const char* sense,
+              const lp_options* opt, lp_problem** out) {
+  try {
+    return create_impl(m, n, nnz, row_ptr, col_idx, val, b, c, lb, ub, sense, opt, out);
+  } catch (const std::exception& ex) {
+    return set_err(nullptr, LP_ERR_OOM, std::string("host exception: ") + ex.what());
+  }
+}
+
+int lp_solve(lp_problem* p, double rel_kkt_tol, int64_t iter_limit, int32_t* status_out) {
+  if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
+  if (!(rel_kkt_tol >= 0.0)) return set_err(p, LP_ERR_INVALID_ARG, "rel_kkt_tol must be >= 0");
+  if (iter_limit < 0) return set_err(p, LP_ERR_INVALID_ARG, "iter_limit must be >= 0");
+  try {
+    return solve_impl(p, rel_kkt_tol, iter_limit, status_out);
+  } catch (const std::exception& ex) {
+    return set_err(p, LP_ERR_OOM, std::string("host exception: ") + ex.what());
+  }
+}
+
+int lp_result(lp_problem* p, double* x, double* y, lp_stats* st) {
+  if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
+  if (!p->solved_once) return set_err(p, LP_ERR_NOT_SOLVED, "lp_result called before lp_solve");
+  TRY(select_device(p));
+  DevState hs;
+  CK(cudaMemcpyAsync(&hs, p->d.st, sizeof(hs), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  TRY(download_vec(p, p->d.x[hs.cur], p->d.dc, p->d.n, p->pcol, x));
+  TRY(download_vec(p, p->d.y[hs.cur], p->d.dr, p->d.m, p->prow, y));
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->pobj = hs.pobj;
+    st->dobj = hs.dobj;
+    st->rel_pres = hs.rel_pres;
+    st->rel_dres = hs.rel_dres;
+    st->rel_gap = hs.rel_gap;
+    st->iterations = hs.attempts;
+    st->accepted = hs.k;
+    st->restarts = hs.restarts;
+    st->eta = hs.eta;
+    st->omega = hs.omega;
+    st->solve_ms = p->last_solve_ms;
+    st->status = p->last_status;
+  }
+  return LP_OK;
+}
+
+int lp_get_iterate(lp_problem* p, double* x, double* y, double* T, double* Sigma, double* scal) {
+  if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
+  TRY(select_device(p));
+  launch_flush_update(p->d, p->prm, p->stream);
+  CK(cudaGetLastError());
+  DevState hs;
+  CK(cudaMemcpyAsync(&hs, p->d.st, sizeof(hs), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  TRY(download_vec(p, p->d.x[hs.cur], nullptr, p->d.n, p->pcol, x));
+  TRY(download_vec(p, p->d.y[hs.cur], nullptr, p->d.m, p->prow, y));
+  TRY(download_vec(p, p->d.T, nullptr, p->d.n, p->pcol, T));
+  TRY(download_vec(p, p->d.S, nullptr, p->d.m, p->prow, Sigma));
+  if (scal) {
+    scal[0] = hs.eta;
+    scal[1] = hs.omega;
+    scal[2] = (double)hs.k;
+    scal[3] = (double)hs.attempts;
+    scal[4] = hs.wsum;
+    scal[5] = (double)hs.restarts;
+    scal[6] = hs.last_eta_max;
+    scal[7] = (double)hs.last_accept;
+  }
+  return LP_OK;
+}
+
+int lp_get_scaling(lp_problem* p, double* dr, double* dc, double* scal) {
+  if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
+  TRY(select_device(p));
+  TRY(download_vec(p, p->d.dr, nullptr, p->d.m, p->prow, dr));
+  TRY(download_vec(p, p->d.dc, nullptr, p->d.n, p->pcol, dc));
+  if (scal) {
+    scal[0] = p->eta0;
+    scal[1] = p->omega0;
+    scal[2] = p->norm_est;
+    scal[3] = p->amax;
+  }
+  return LP_OK;
+}
+
+int lp_reset(lp_problem* p) {
+  if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
+  TRY(select_device(p));
+  return init_state(p);
+}
+
+int lp_kernel_times(lp_problem* p, double* ms, int64_t* samples, int32_t n_kernels, int64_t* launches) {
+  if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
+  if (n_kernels < 0) return set_err(p, LP_ERR_INVALID_ARG, "n_kernels must be >= 0");
+  for (int k = 0; k < n_kernels; ++k) {
+    if (ms) ms[k] = k < 2 ? p->kt_ms[k] : 0.0;
+    if (samples) samples[k] = k < 2 ? p->kt_n[k] : 0;
+  }
+  if (launches) *launches = p->launches;
+  return LP_OK;
+}
+
+void lp_destroy(lp_problem* p) { release(p); }
+
+}  // extern "C"
+
+namespace lpop {
+
+namespace {
+__global__ void mul_into_kernel(double* out, const double* a, const double* f, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] * f[i];
+}
+}  // namespace
+
+void launch_mul_into(double* out, const double* a, const double* f, int n, cudaStream_t s) {
+  int g = (n + kBlock - 1) / kBlock;
+  if (g > 1024) g = 1024;
+  if (g < 1) g = 1;
+  mul_into_kernel<<<g, kBlock, 0, s>>>(out, a, f, n);
+}
+
+}  // namespace lpop

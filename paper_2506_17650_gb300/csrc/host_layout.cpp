@@ -1,0 +1,187 @@
+#include "host_layout.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "../../include/lpop.h"
+
+namespace lpop {
+
+namespace {
+
+// Work order of the bins: whole-block rows first (they are the longest, so
+// they start early), then 32, 16, ... 1 lanes.
+int bin_rank(int width) {
+  switch (width) {
+    case 0: return 0;
+    case 32: return 1;
+    case 16: return 2;
+    case 8: return 3;
+    case 4: return 4;
+    case 2: return 5;
+    default: return 6;
+  }
+}
+
+constexpr long long kBlockRowThreshold = 1024;  // rows longer than this get a whole block
+
+// Stable permutation of rows by bin rank.
+std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<int>& widths_sorted) {
+  const int rows = (int)len.size();
+  std::vector<int> width(rows);
+  for (int r = 0; r < rows; ++r) width[r] = width_for_length(len[r]);
+  std::vector<int> perm(rows);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return bin_rank(width[a]) < bin_rank(width[b]); });
+  widths_sorted.resize(rows);
+  for (int r = 0; r < rows; ++r) widths_sorted[r] = width[perm[r]];
+  return perm;
+}
+
+}  // namespace
+
+int width_for_length(long long len) {
+  if (len <= 2) return 1;
+  if (len <= 4) return 2;
+  if (len <= 8) return 4;
+  if (len <= 16) return 8;
+  if (len <= 32) return 16;
+  if (len <= kBlockRowThreshold) return 32;
+  return 0;
+}
+
+BinTable make_bins(const std::vector<int>& widths_sorted) {
+  BinTable t{};
+  t.nbins = 0;
+  t.nunits = 0;
+  const int rows = (int)widths_sorted.size();
+  int r = 0;
+  while (r < rows) {
+    const int w = widths_sorted[r];
+    int e = r;
+    while (e < rows && widths_sorted[e] == w) ++e;
+    Bin& b = t.bin[t.nbins++];
+    b.row_begin = r;
+    b.row_end = e;
+    b.width = w;
+    b.unit_begin = t.nunits;
+    const int per = w == 0 ? 1 : kBlock / w;
+    t.nunits += (e - r + per - 1) / per;
+    r = e;
+  }
+  return t;
+}
+
+int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* val, HostLayout& out, std::string& err) {
+  if (m < 0 || n < 1 || nnz < 0) {
+    err = "need m >= 0, n >= 1 and nnz >= 0";
+    return LP_ERR_INVALID_ARG;
+  }
+  if (nnz >= (int64_t)1 << 31) {
+    err = "nnz must be below 2^31";
+    return LP_ERR_INVALID_ARG;
+  }
+  if (!row_ptr || (nnz > 0 && (!col_idx || !val))) {
+    err = "row_ptr, col_idx and val must not be NULL";
+    return LP_ERR_INVALID_ARG;
+  }
+  if (row_ptr[0] != 0 || row_ptr[m] != nnz) {
+    err = "row_ptr[0] must be 0 and row_ptr[m] must equal nnz";
+    return LP_ERR_INVALID_INPUT;
+  }
+  for (int i = 0; i < m; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) {
+      err = "row_ptr must be non-decreasing (row " + std::to_string(i) + ")";
+      return LP_ERR_INVALID_INPUT;
+    }
+  }
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (col_idx[k] < 0 || col_idx[k] >= n) {
+      err = "col_idx[" + std::to_string(k) + "] out of range";
+      return LP_ERR_INVALID_INPUT;
+    }
+    if (!std::isfinite(val[k])) {
+      err = "val[" + std::to_string(k) + "] is not finite";
+      return LP_ERR_INVALID_INPUT;
+    }
+  }
+
+  // sort each row by column and merge repeated entries (summed)
+  std::vector<int64_t> rp(m + 1, 0);
+  std::vector<int> ci;
+  std::vector<double> cv;
+  ci.reserve(nnz);
+  cv.reserve(nnz);
+  std::vector<std::pair<int, double>> row;
+  for (int i = 0; i < m; ++i) {
+    row.clear();
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) row.emplace_back(col_idx[k], val[k]);
+    std::stable_sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (size_t t = 0; t < row.size();) {
+      const int c = row[t].first;
+      double s = row[t].second;
+      size_t e = t + 1;
+      while (e < row.size() && row[e].first == c) s += row[e++].second;
+      ci.push_back(c);
+      cv.push_back(s);
+      t = e;
+    }
+    rp[i + 1] = (int64_t)ci.size();
+  }
+  const long long nz = (long long)ci.size();
+
+  std::vector<long long> rlen(m), clen(n, 0);
+  for (int i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
+  for (long long k = 0; k < nz; ++k) clen[ci[k]]++;
+
+  std::vector<int> wA, wAt;
+  out.m = m;
+  out.n = n;
+  out.nnz = nz;
+  out.prow = bin_permutation(rlen, wA);
+  out.pcol = bin_permutation(clen, wAt);
+  out.binsA = make_bins(wA);
+  out.binsAt = make_bins(wAt);
+  std::vector<int> icol(n);
+  for (int j = 0; j < n; ++j) icol[out.pcol[j]] = j;
+
+  // permuted CSR of A, rows in bin order, column indices permuted and sorted
+  out.A_rp.assign(m + 1, 0);
+  out.A_ci.resize(nz);
+  out.A_v.resize(nz);
+  std::vector<std::pair<int, double>> tmp;
+  int64_t pos = 0;
+  for (int ip = 0; ip < m; ++ip) {
+    const int i = out.prow[ip];
+    tmp.clear();
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) tmp.emplace_back(icol[ci[k]], cv[k]);
+    std::sort(tmp.begin(), tmp.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    for (const auto& e : tmp) {
+      out.A_ci[pos] = e.first;
+      out.A_v[pos] = e.second;
+      ++pos;
+    }
+    out.A_rp[ip + 1] = (int)pos;
+  }
+
+  // permuted CSR of A^T by counting sort (row indices come out sorted)
+  out.At_rp.assign(n + 1, 0);
+  for (long long k = 0; k < nz; ++k) out.At_rp[out.A_ci[k] + 1]++;
+  for (int j = 0; j < n; ++j) out.At_rp[j + 1] += out.At_rp[j];
+  out.At_ci.resize(nz);
+  out.At_v.resize(nz);
+  std::vector<int> fillp(out.At_rp.begin(), out.At_rp.end() - 1);
+  for (int ip = 0; ip < m; ++ip) {
+    for (int k = out.A_rp[ip]; k < out.A_rp[ip + 1]; ++k) {
+      const int j = out.A_ci[k];
+      out.At_ci[fillp[j]] = ip;
+      out.At_v[fillp[j]] = out.A_v[k];
+      fillp[j]++;
+    }
+  }
+  return LP_OK;
+}
+
+}  // namespace lpop

@@ -1,0 +1,35 @@
+// Host-side data layout of a problem: input validation, duplicate merging,
+// and the permuted ("bin order") CSR copies of A and A^T.  Pure C++: no CUDA
+// calls, so it runs (and is tested) without a GPU.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "layout_types.h"
+
+namespace lpop {
+
+struct HostLayout {
+  int m = 0, n = 0;
+  long long nnz = 0;  // after merging repeated entries
+  std::vector<int> prow, pcol;  // permuted index -> caller's index
+  std::vector<int> A_rp, A_ci, At_rp, At_ci;
+  std::vector<double> A_v, At_v;
+  BinTable binsA{}, binsAt{};
+};
+
+// Lanes per row for a row of length len: 1, 2, 4, ..., 32, or 0 (a block per row).
+int width_for_length(long long len);
+
+// Validate the CSR input and build the layout.  Returns 0 on success, or a
+// negative lp_err code with a message in err.
+int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* val, HostLayout& out, std::string& err);
+
+// Bin table for rows already sorted by bin (widths non-increasing in "work" order).
+BinTable make_bins(const std::vector<int>& widths_sorted);
+
+}  // namespace lpop

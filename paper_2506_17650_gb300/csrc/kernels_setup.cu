@@ -1,0 +1,243 @@
+// Preprocessing kernels (run once per problem by lp_create, and by lp_reset
+// for the initial state):
+//   - Ruiz equilibration (Section 2): row / column infinity norms, factors
+//     1/sqrt(norm), applied to both CSR copies;
+//   - Pock-Chambolle rescaling (Section 2): factors 1/sqrt(sum |a|^beta) for
+//     rows and 1/sqrt(sum |a|^(2-beta)) for columns;
+//   - L2 rescaling (Section 4.2): factors 1/sqrt(||row||_2), 1/sqrt(||col||_2);
+//   - rescaling of b, c, l, u; norms; max |a_ij|; power iteration for ||A~||_2;
+//   - the initial iterate x_0 = proj_[l,u](0), y_0 = 0, T_0 = Sigma_0 = I (Section 3.2).
+// Reductions use per-block partials summed by one block in a fixed order.
+#include "common.cuh"
+#include "spmv.cuh"
+
+namespace lpop {
+
+namespace {
+
+constexpr int kSetupGrid = 1024;
+
+__global__ void fill_kernel(double* v, double val, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[i] = val;
+}
+
+// one warp per row: out[r] = max_k |v_k|
+__global__ void row_absmax_kernel(Csr M, int rows, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    double mx = 0.0;
+    for (int k = M.rp[r] + lane; k < M.rp[r + 1]; k += 32) mx = fmax(mx, fabs(M.v[k]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) out[r] = mx;
+  }
+}
+
+// one warp per row: out[r] = sum_k |v_k|^beta (beta == 1 and beta == 2 exact), optionally sqrt
+__global__ void row_powsum_kernel(Csr M, int rows, double beta, int square_root, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    double s = 0.0;
+    for (int k = M.rp[r] + lane; k < M.rp[r + 1]; k += 32) {
+      const double a = fabs(M.v[k]);
+      s += beta == 1.0 ? a : (beta == 2.0 ? a * a : (beta == 0.0 ? 1.0 : pow(a, beta)));
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) out[r] = square_root ? sqrt(s) : s;
+  }
+}
+
+__global__ void factor_kernel(double* f, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double v = f[i];
+    f[i] = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+  }
+}
+
+// v_k <- (v_k * frow_i) * fcol_j for entry (i, j) of A.  For the A copy the
+// row is i and ci is j; for the A^T copy the row is j and ci is i.  Both
+// copies evaluate the same expression, so they stay bitwise equal.
+__global__ void scale_values_kernel(const int* rp, const int* ci, double* v, int rows, const double* frow,
+                                    const double* fcol, int row_is_a_row) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) {
+      const int c = ci[k];
+      const int i = row_is_a_row ? r : c;
+      const int j = row_is_a_row ? c : r;
+      v[k] = (v[k] * frow[i]) * fcol[j];
+    }
+  }
+}
+
+__global__ void mul_kernel(double* a, const double* f, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] *= f[i];
+}
+
+__global__ void scale_vectors_kernel(Dev d) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) d.b[i] = d.dr[i] * d.b[i];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
+    const double f = d.dc[j];
+    d.c[j] = f * d.c[j];
+    d.l[j] = d.l[j] / f;
+    d.u[j] = d.u[j] / f;
+  }
+}
+
+__global__ void sumsq_partial_kernel(const double* v, long long n, double* part) {
+  __shared__ double smem[32];
+  double s[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s[0] += v[i] * v[i];
+  block_sum<1>(s, smem);
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void absmax_partial_kernel(const double* v, long long n, double* part) {
+  __shared__ double smem[32];
+  double mx = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs(v[i]));
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) smem[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, smem[w]);
+    part[blockIdx.x] = t;
+  }
+}
+
+// out[0] = sqrt(sum part) (mode 0) or max part (mode 1); one block, fixed order
+__global__ void finish_kernel(const double* part, int np, double* out, int mode) {
+  __shared__ double smem[32];
+  double s[1] = {0.0};
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s[0] = mode == 0 ? s[0] + part[i] : fmax(s[0], part[i]);
+  if (mode == 0) {
+    block_sum<1>(s, smem);
+    if (threadIdx.x == 0) out[0] = sqrt(s[0]);
+  } else {
+    for (int off = 16; off > 0; off >>= 1) s[0] = fmax(s[0], __shfl_xor_sync(0xffffffffu, s[0], off));
+    if ((threadIdx.x & 31) == 0) smem[threadIdx.x >> 5] = s[0];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, smem[w]);
+      out[0] = t;
+    }
+  }
+}
+
+__global__ void scale_by_inv_kernel(double* v, int n, const double* denom) {
+  const double dv = denom[0];
+  if (dv == 0.0) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = v[i] / dv;
+}
+
+struct StoreOp {
+  double* y;
+  __device__ __forceinline__ void row(int r, const double (&s)[1]) { y[r] = s[0]; }
+};
+
+__global__ void __launch_bounds__(kBlock) spmv_kernel(Csr M, BinTable bt, const double* x, double* y) {
+  __shared__ double smem[32];
+  StoreOp op{y};
+  Gather<1> g;
+  g.x[0] = x;
+  for_each_row<1>(bt, M, g, op, smem);
+}
+
+__global__ void init_vectors_kernel(Dev d) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
+    const double x0 = fmin(fmax(0.0, d.l[j]), d.u[j]);
+    d.x[0][j] = x0; d.x[1][j] = x0;
+    d.xbar[0][j] = 0.0; d.xbar[1][j] = 0.0;
+    d.T[j] = 1.0; d.GT[j] = 0.0; d.q[j] = 0.0;
+    d.x_last[j] = x0;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) {
+    d.y[0][i] = 0.0; d.y[1][i] = 0.0;
+    d.ybar[0][i] = 0.0; d.ybar[1][i] = 0.0;
+    d.S[i] = 1.0; d.GS[i] = 0.0; d.p[i] = 0.0;
+    d.y_last[i] = 0.0;
+    d.ax_avg[i] = 0.0;
+  }
+}
+
+int grid_for(long long n) {
+  long long g = (n + kBlock - 1) / kBlock;
+  if (g > kSetupGrid) g = kSetupGrid;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int warp_grid_for(long long rows) {
+  long long g = (rows * 32 + kBlock - 1) / kBlock;
+  if (g > 4 * kSetupGrid) g = 4 * kSetupGrid;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+// BinTable for a CSR matrix used only by spmv_kernel when no table is at hand
+}  // namespace
+
+void launch_fill(double* v, double val, long long n, cudaStream_t s) {
+  if (n > 0) fill_kernel<<<grid_for(n), kBlock, 0, s>>>(v, val, n);
+}
+
+void launch_row_absmax(const Csr& M, int rows, double* out, cudaStream_t s) {
+  if (rows > 0) row_absmax_kernel<<<warp_grid_for(rows), kBlock, 0, s>>>(M, rows, out);
+}
+
+void launch_row_powsum(const Csr& M, int rows, double beta, int square_root, double* out, cudaStream_t s) {
+  if (rows > 0) row_powsum_kernel<<<warp_grid_for(rows), kBlock, 0, s>>>(M, rows, beta, square_root, out);
+}
+
+void launch_factor_from_norm(double* f, int n, cudaStream_t s) {
+  if (n > 0) factor_kernel<<<grid_for(n), kBlock, 0, s>>>(f, n);
+}
+
+void launch_scale_values(int* rp, int* ci, double* v, int rows, const double* frow, const double* fcol,
+                         int row_is_a_row, cudaStream_t s) {
+  if (rows > 0) scale_values_kernel<<<warp_grid_for(rows), kBlock, 0, s>>>(rp, ci, v, rows, frow, fcol, row_is_a_row);
+}
+
+void launch_mul_inplace(double* a, const double* f, int n, cudaStream_t s) {
+  if (n > 0) mul_kernel<<<grid_for(n), kBlock, 0, s>>>(a, f, n);
+}
+
+void launch_scale_problem_vectors(const Dev& d, cudaStream_t s) {
+  scale_vectors_kernel<<<grid_for(d.n > d.m ? d.n : d.m), kBlock, 0, s>>>(d);
+}
+
+// out[0] = ||v||_2 ; uses out[1 .. 1 + kSetupGrid) as partials
+void launch_norm2(const double* v, int n, double* out, cudaStream_t s) {
+  const int g = grid_for(n);
+  sumsq_partial_kernel<<<g, kBlock, 0, s>>>(v, n, out + 1);
+  finish_kernel<<<1, kBlock, 0, s>>>(out + 1, g, out, 0);
+}
+
+void launch_absmax(const double* v, long long n, double* out, cudaStream_t s) {
+  const int g = grid_for(n);
+  absmax_partial_kernel<<<g, kBlock, 0, s>>>(v, n, out + 1);
+  finish_kernel<<<1, kBlock, 0, s>>>(out + 1, g, out, 1);
+}
+
+void launch_scale_by_inv(double* v, int n, const double* denom, cudaStream_t s) {
+  if (n > 0) scale_by_inv_kernel<<<grid_for(n), kBlock, 0, s>>>(v, n, denom);
+}
+
+void launch_spmv_binned(const Csr& M, const BinTable& bt, int grid, const double* x, double* y, cudaStream_t s) {
+  if (bt.nunits > 0) spmv_kernel<<<grid, kBlock, 0, s>>>(M, bt, x, y);
+}
+
+void launch_init_vectors(const Dev& d, cudaStream_t s) {
+  init_vectors_kernel<<<grid_for(d.n > d.m ? d.n : d.m), kBlock, 0, s>>>(d);
+}
+
+}  // namespace lpop

@@ -1,0 +1,35 @@
+// Plain layout types shared by host-only and device code (no CUDA headers).
+#pragma once
+
+#include <stdint.h>
+
+namespace lpop {
+
+constexpr int kBlock = 256;      // threads per block of every row kernel
+constexpr int kMaxBins = 8;      // row-length classes per matrix
+constexpr int kMaxPartials = 12; // per-block partial sums per kernel
+constexpr int kPrimalTimed = 0;  // kernel ids for the event timers
+constexpr int kDualTimed = 1;
+
+enum Sense : uint8_t { kEq = 0, kLe = 1, kGe = 2 };
+enum Mode : int { kPlain = 0, kPdlp = 1 };
+enum Sched : int { kAdagrad = 0, kAdagradNorm = 1, kConst = 2 };
+
+// One row-length class: rows [row_begin, row_end) of a permuted CSR matrix,
+// handled with `width` lanes per row (1..32), or a whole block per row when
+// width == 0.  Work units: one row per unit for width 0, kBlock/width rows
+// per unit otherwise; units of all bins are numbered consecutively.
+struct Bin {
+  int row_begin;
+  int row_end;
+  int width;
+  int unit_begin;
+};
+
+struct BinTable {
+  int nbins;
+  int nunits;
+  Bin bin[kMaxBins];
+};
+
+}  // namespace lpop
