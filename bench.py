@@ -220,6 +220,7 @@ def gpu_arm(args):
     opts = dict(alpha=ALPHA, phi=PHI, normalize=1, kernel_timing=1, device=local, stream=stream.cuda_stream)
     prob = lpop.Problem(lp, **opts)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    _, _, layout = prob.scaling()
 
     def one_solve(timed):
         prob.reset()
@@ -335,6 +336,7 @@ def gpu_arm(args):
                 "samples": int(kt_n[0]),
             },
             "gpu_launches": launches_total,
+            "launch_layout": {k: layout[k] for k in ("grid_a", "grid_at", "units_a", "units_at")},
             "clocks": clk,
             "wall_s": wall,
             "fixed_precond": fixed,

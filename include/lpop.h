@@ -167,11 +167,32 @@ int lp_get_iterate(lp_problem* p, double* x, double* y, double* T, double* Sigma
 
 /*
  * Scaled-space vectors of the preprocessing, caller's order: dr (double[m]),
- * dc (double[n]) with A~ = diag(dr) A diag(dc), and scal (double[4], may be
- * NULL) = {eta_0, omega_0, ||A~||_2 estimate (plain mode, else 0), max|A~_ij|}.
+ * dc (double[n]) with A~ = diag(dr) A diag(dc), and scal (double[8], may be
+ * NULL) = {eta_0, omega_0, ||A~||_2 estimate (plain mode, else 0), max|A~_ij|,
+ * blocks of the A-row kernels, blocks of the A^T-row kernels, work units of A,
+ * work units of A^T}.
  * Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
  */
 int lp_get_scaling(lp_problem* p, double* dr, double* dc, double* scal);
+
+/*
+ * Checkpoint / resume: the complete iteration state in the PREPROCESSED space,
+ * caller's order.  A pending preconditioner update is applied before export.
+ *   vec_n  double[5 n]: x, xbar (eta-weighted sum since the last restart),
+ *          T, AdaGrad accumulator of T, x at the last restart
+ *   vec_m  double[6 m]: y, ybar, A x, Sigma, AdaGrad accumulator of Sigma,
+ *          y at the last restart
+ *   scal   double[16]: eta, omega, wsum, scalar AdaGrad accumulators (primal,
+ *          dual), weighted-KKT parts at the last restart (||pres||^2,
+ *          ||dres||^2, gap^2), weighted KKT of the previous check, k,
+ *          attempts, attempt of the last restart, restarts, restart reference
+ *          recorded (0/1), initial check done (0/1), 0
+ * lp_set_state takes the same layout (all three arrays required) and makes it
+ * the state the next lp_solve continues from; the iteration limit of lp_solve
+ * stays cumulative in `attempts`.  Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
+ */
+int lp_get_state(lp_problem* p, double* vec_n, double* vec_m, double* scal);
+int lp_set_state(lp_problem* p, const double* vec_n, const double* vec_m, const double* scal);
 
 /*
  * Return the problem to its initial state (x_0 = proj(0), y_0 = 0, T = Sigma = I,

@@ -116,6 +116,10 @@ def load_library(path: str | None = None):
     lib.lp_get_iterate.restype = c_int32
     lib.lp_get_scaling.argtypes = [c_void_p, _DP, _DP, _DP]
     lib.lp_get_scaling.restype = c_int32
+    lib.lp_get_state.argtypes = [c_void_p, _DP, _DP, _DP]
+    lib.lp_get_state.restype = c_int32
+    lib.lp_set_state.argtypes = [c_void_p, _DP, _DP, _DP]
+    lib.lp_set_state.restype = c_int32
     lib.lp_reset.argtypes = [c_void_p]
     lib.lp_reset.restype = c_int32
     lib.lp_kernel_times.argtypes = [c_void_p, _DP, POINTER(c_int64), c_int32, POINTER(c_int64)]
@@ -204,11 +208,40 @@ def lp_get_iterate(handle, m, n):
 
 
 def lp_get_scaling(handle, m, n):
-    """(dr, dc, dict(eta0, omega0, norm_est, amax)) with A~ = diag(dr) A diag(dc)."""
-    dr, dc, scal = _out(m), _out(n), _out(4)
+    """(dr, dc, dict(eta0, omega0, norm_est, amax, grid sizes, work units)) with A~ = diag(dr) A diag(dc)."""
+    dr, dc, scal = _out(m), _out(n), _out(8)
     _check(load_library().lp_get_scaling(handle, _ptr(dr, c_double), _ptr(dc, c_double), _ptr(scal, c_double)),
            handle)
-    return dr, dc, dict(eta0=scal[0], omega0=scal[1], norm_est=scal[2], amax=scal[3])
+    return dr, dc, dict(eta0=scal[0], omega0=scal[1], norm_est=scal[2], amax=scal[3], grid_a=int(scal[4]),
+                        grid_at=int(scal[5]), units_a=int(scal[6]), units_at=int(scal[7]))
+
+
+STATE_N = ("x", "xbar", "T", "GT", "x_last")
+STATE_M = ("y", "ybar", "ax", "Sigma", "GS", "y_last")
+STATE_SCAL = ("eta", "omega", "wsum", "gp_norm", "gd_norm", "klast_p2", "klast_d2", "klast_g2", "k_prev", "k",
+              "attempts", "last_restart_attempt", "restarts", "refs_set", "initial_check_done")
+_STATE_INT = {"k", "attempts", "last_restart_attempt", "restarts", "refs_set", "initial_check_done"}
+
+
+def lp_get_state(handle, m, n):
+    """Complete scaled-space state (checkpoint): dict of the STATE_N / STATE_M vectors and STATE_SCAL scalars."""
+    vn, vm, scal = _out(5 * n), _out(6 * m), _out(16)
+    _check(load_library().lp_get_state(handle, _ptr(vn, c_double), _ptr(vm, c_double), _ptr(scal, c_double)), handle)
+    out = {k: vn[i * n:(i + 1) * n].copy() for i, k in enumerate(STATE_N)}
+    out.update({k: vm[i * m:(i + 1) * m].copy() for i, k in enumerate(STATE_M)})
+    out.update({k: (int(scal[i]) if k in _STATE_INT else float(scal[i])) for i, k in enumerate(STATE_SCAL)})
+    return out
+
+
+def lp_set_state(handle, m, n, state):
+    """Resume from a state dict with the keys of lp_get_state."""
+    vn = np.ascontiguousarray(np.concatenate([np.asarray(state[k], dtype=np.float64).reshape(n) for k in STATE_N]))
+    vm = np.ascontiguousarray(np.concatenate([np.asarray(state[k], dtype=np.float64).reshape(m) for k in STATE_M])) \
+        if m > 0 else np.zeros(1)
+    scal = np.zeros(16)
+    for i, k in enumerate(STATE_SCAL):
+        scal[i] = float(state[k])
+    _check(load_library().lp_set_state(handle, _ptr(vn, c_double), _ptr(vm, c_double), _ptr(scal, c_double)), handle)
 
 
 def lp_reset(handle):
@@ -261,6 +294,12 @@ class Problem:
 
     def reset(self):
         lp_reset(self.handle)
+
+    def get_state(self):
+        return lp_get_state(self.handle, self.m, self.n)
+
+    def set_state(self, state):
+        lp_set_state(self.handle, self.m, self.n, state)
 
     def kernel_times(self):
         return lp_kernel_times(self.handle)

@@ -368,6 +368,81 @@ int download_vec(lp_problem* p, const double* dsrc, const double* dscale, int le
   return LP_OK;
 }
 
+int upload_vec(lp_problem* p, double* ddst, const double* host, int len, const std::vector<int>& perm) {
+  if (len == 0) return LP_OK;
+  std::vector<double> h(len);
+  for (int i = 0; i < len; ++i) h[i] = host[perm[i]];
+  CK(cudaMemcpyAsync(ddst, h.data(), sizeof(double) * len, cudaMemcpyHostToDevice, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return LP_OK;
+}
+
+int get_state_impl(lp_problem* p, double* vn, double* vm, double* scal) {
+  TRY(select_device(p));
+  launch_flush_update(p->d, p->prm, p->stream);
+  CK(cudaGetLastError());
+  DevState hs;
+  CK(cudaMemcpyAsync(&hs, p->d.st, sizeof(hs), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  const int n = p->d.n, m = p->d.m, c = hs.cur;
+  const Dev& d = p->d;
+  if (vn) {
+    const double* src[5] = {d.x[c], d.xbar[c], d.T, d.GT, d.x_last};
+    for (int k = 0; k < 5; ++k) TRY(download_vec(p, src[k], nullptr, n, p->pcol, vn + (size_t)k * n));
+  }
+  if (vm) {
+    const double* src[6] = {d.y[c], d.ybar[c], d.ax[c], d.S, d.GS, d.y_last};
+    for (int k = 0; k < 6; ++k) TRY(download_vec(p, src[k], nullptr, m, p->prow, vm + (size_t)k * m));
+  }
+  if (scal) {
+    const double v[16] = {hs.eta, hs.omega, hs.wsum, hs.gp_norm, hs.gd_norm, hs.klast_p2, hs.klast_d2,
+                          hs.klast_g2, hs.k_prev, (double)hs.k, (double)hs.attempts,
+                          (double)hs.last_restart_attempt, (double)hs.restarts, (double)hs.checked0,
+                          p->initial_check_done ? 1.0 : 0.0, 0.0};
+    std::memcpy(scal, v, sizeof(v));
+  }
+  return LP_OK;
+}
+
+int set_state_impl(lp_problem* p, const double* vn, const double* vm, const double* scal) {
+  TRY(select_device(p));
+  CK(cudaStreamSynchronize(p->stream));
+  DevState hs;
+  CK(cudaMemcpyAsync(&hs, p->d.st, sizeof(hs), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  const int n = p->d.n, m = p->d.m, c = hs.cur;
+  const Dev& d = p->d;
+  double* dn[5] = {d.x[c], d.xbar[c], d.T, d.GT, d.x_last};
+  for (int k = 0; k < 5; ++k) TRY(upload_vec(p, dn[k], vn + (size_t)k * n, n, p->pcol));
+  double* dm[6] = {d.y[c], d.ybar[c], d.ax[c], d.S, d.GS, d.y_last};
+  for (int k = 0; k < 6; ++k) TRY(upload_vec(p, dm[k], vm + (size_t)k * m, m, p->prow));
+  hs.eta = scal[0];
+  hs.omega = scal[1];
+  hs.wsum = scal[2];
+  hs.gp_norm = scal[3];
+  hs.gd_norm = scal[4];
+  hs.klast_p2 = scal[5];
+  hs.klast_d2 = scal[6];
+  hs.klast_g2 = scal[7];
+  hs.k_prev = scal[8];
+  hs.k = (long long)scal[9];
+  hs.attempts = (long long)scal[10];
+  hs.last_restart_attempt = (long long)scal[11];
+  hs.restarts = (long long)scal[12];
+  hs.checked0 = scal[13] != 0.0;
+  hs.pend_p = hs.pend_d = 0;
+  hs.status = 0;
+  hs.counter = 0;
+  hs.restart_action = 0;
+  hs.adopt_avg = 0;
+  CK(cudaMemcpyAsync(p->d.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  p->host_attempts = hs.attempts;
+  p->initial_check_done = scal[14] != 0.0;
+  p->solved_once = false;
+  return LP_OK;
+}
+
 void release(lp_problem* p) {
   if (!p) return;
   cudaSetDevice(p->device);
@@ -643,8 +718,31 @@ int lp_get_scaling(lp_problem* p, double* dr, double* dc, double* scal) {
     scal[1] = p->omega0;
     scal[2] = p->norm_est;
     scal[3] = p->amax;
+    scal[4] = p->d.gridA;
+    scal[5] = p->d.gridAt;
+    scal[6] = p->d.binsA.nunits;
+    scal[7] = p->d.binsAt.nunits;
   }
   return LP_OK;
+}
+
+int lp_get_state(lp_problem* p, double* vec_n, double* vec_m, double* scal) {
+  if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
+  try {
+    return get_state_impl(p, vec_n, vec_m, scal);
+  } catch (const std::exception& ex) {
+    return set_err(p, LP_ERR_OOM, std::string("host exception: ") + ex.what());
+  }
+}
+
+int lp_set_state(lp_problem* p, const double* vec_n, const double* vec_m, const double* scal) {
+  if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
+  if (!vec_n || !scal || (!vec_m && p->d.m > 0)) return set_err(p, LP_ERR_INVALID_ARG, "state arrays must not be NULL");
+  try {
+    return set_state_impl(p, vec_n, vec_m, scal);
+  } catch (const std::exception& ex) {
+    return set_err(p, LP_ERR_OOM, std::string("host exception: ") + ex.what());
+  }
 }
 
 int lp_reset(lp_problem* p) {

@@ -167,10 +167,7 @@ __device__ void check_control(const Dev& d, const Params& prm, const double (&p1
       return;
     }
   }
-  if (prm.mode != kPdlp) {
-    st->checked0 = 1;
-    return;
-  }
+  if (prm.mode != kPdlp) return;  // plain mode: no restarts, no restart reference
   const double omega = st->omega;
   if (!st->checked0) {
     st->klast_p2 = cd[0].p2; st->klast_d2 = cd[0].d2; st->klast_g2 = cd[0].g2;
