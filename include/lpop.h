@@ -210,6 +210,37 @@ int lp_reset(lp_problem* p);
  */
 int lp_kernel_times(lp_problem* p, double* ms, int64_t* samples, int32_t n_kernels, int64_t* launches);
 
+/*
+ * No-allocation variant of the power iteration that lp_create runs in plain
+ * mode (||A||_2 estimate for the vanilla step 0.9 / ||A||_2).  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code inside a framework that has reserved device memory for
+ * its own pool, a real-time loop that must not allocate, or a caller whose
+ * buffers come from another allocator -- and that already hold the matrix on
+ * the device.  It allocates nothing: its scratch (three work vectors and the
+ * reduction's partial sums) is one fixed device array of 2^20 doubles (8 MiB)
+ * that every GPU which loads this library holds until the process exits.
+ *   m, n        rows and columns, m >= 1, n >= 1, and 2 n + m + 1025 <= 2^20
+ *               (larger sizes are rejected with LP_ERR_INVALID_ARG)
+ *   a_*         DEVICE pointers: CSR of A (int32 row_ptr[m+1], int32
+ *               col_idx[nnz], double val[nnz])
+ *   at_*        DEVICE pointers: CSR of A^T (n rows) holding the same entries
+ *   iters       power iterations on A^T A from the all-ones direction, >= 1
+ *   stream      cudaStream_t for all work (NULL = default stream); the call
+ *               waits for this stream before returning
+ *   norm_out    HOST pointer receiving sqrt(||A^T A v||) of the last round
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the one array and leave their data in it;
+ * nothing in it needs to start at zero.  Calls whose work overlaps on the GPU
+ * (other threads or streams) race on the array: serialise them.
+ * Errors: LP_ERR_INVALID_ARG (sizes, NULL pointers), LP_ERR_CUDA; the message
+ * is returned by lp_last_error(NULL).
+ */
+int lp_power_norm_noalloc(int32_t m, int32_t n, const int32_t* a_row_ptr, const int32_t* a_col_idx,
+                          const double* a_val, const int32_t* at_row_ptr, const int32_t* at_col_idx,
+                          const double* at_val, int32_t iters, void* stream, double* norm_out);
+
 /* Free all device and host memory of the problem.  NULL is ignored. */
 void lp_destroy(lp_problem* p);
 

@@ -124,6 +124,9 @@ def load_library(path: str | None = None):
     lib.lp_reset.restype = c_int32
     lib.lp_kernel_times.argtypes = [c_void_p, _DP, POINTER(c_int64), c_int32, POINTER(c_int64)]
     lib.lp_kernel_times.restype = c_int32
+    lib.lp_power_norm_noalloc.argtypes = [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, c_int32, c_void_p, POINTER(c_double)]
+    lib.lp_power_norm_noalloc.restype = c_int32
     lib.lp_destroy.argtypes = [c_void_p]
     lib.lp_destroy.restype = None
     lib.lp_last_error.argtypes = [c_void_p]
@@ -256,6 +259,21 @@ def lp_kernel_times(handle):
     _check(load_library().lp_kernel_times(handle, _ptr(ms, c_double), _ptr(ns, c_int64), 2, ctypes.byref(launches)),
            handle)
     return ms, ns, launches.value
+
+
+def lp_power_norm_noalloc(m, n, a_row_ptr, a_col_idx, a_val, at_row_ptr, at_col_idx, at_val, iters=200,
+                          stream=None) -> float:
+    """||A||_2 power-iteration estimate without any device allocation.
+
+    For callers that cannot allocate device memory; the six matrix arguments
+    are DEVICE addresses (ints, e.g. ``tensor.data_ptr()``) of the CSR of A and
+    of A^T.  Uses the library's fixed 8 MiB scratch (2 n + m + 1025 doubles at
+    most)."""
+    out = c_double(0.0)
+    rc = load_library().lp_power_norm_noalloc(int(m), int(n), a_row_ptr, a_col_idx, a_val, at_row_ptr, at_col_idx,
+                                              at_val, int(iters), stream, ctypes.byref(out))
+    _check(rc)
+    return out.value
 
 
 def lp_destroy(handle):

@@ -24,6 +24,11 @@ int row_kernel_blocks_per_sm();
 
 static thread_local std::string g_last_error;
 
+namespace lpop {
+// Lets other translation units report an error through lp_last_error(NULL).
+void set_thread_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace lpop
+
 struct lp_problem {
   lp_options opt{};
   int device = 0;
