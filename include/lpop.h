@@ -64,6 +64,13 @@ enum {
   LP_MODE_PDLP = 1   /* Eq. (6): adaptive step size, primal weight, restarts (Section 3.2) */
 };
 
+/* options.precision */
+enum {
+  LP_PREC_FP64 = 0,  /* every kernel in FP64 */
+  LP_PREC_MIXED = 1  /* FP32 matrix values, vectors and row arithmetic; FP64 KKT / step-size /
+                        normalisation reductions and scalars; FP64 refinement phase */
+};
+
 /* options.scheduler: learning-rate rule of the online update (Section 4.1 names AdaGrad) */
 enum {
   LP_SCHED_ADAGRAD = 0,      /* per-coordinate AdaGrad */
@@ -89,6 +96,10 @@ typedef struct lp_options {
   int32_t kernel_timing;     /* time sampled launches of the hot kernels with CUDA events; default 0 */
   int32_t device;            /* CUDA device ordinal; -1 = the calling thread's current device */
   void* stream;              /* cudaStream_t every launch and copy goes to; NULL = default stream */
+  int32_t precision;         /* LP_PREC_*; default LP_PREC_FP64 */
+  double refine_tol;         /* mixed: the FP32 phase hands over to FP64 once the relative KKT
+                                error is at most this, or after 3 checks without a 10% gain;
+                                default 1e-6 */
   int32_t reserved[8];       /* must be zero */
 } lp_options;
 

@@ -33,6 +33,9 @@ LP_NUMERICAL_ERROR = 4
 LP_MODE_PLAIN = 0
 LP_MODE_PDLP = 1
 
+LP_PREC_FP64 = 0
+LP_PREC_MIXED = 1
+
 LP_SCHED_ADAGRAD = 0
 LP_SCHED_ADAGRAD_NORM = 1
 LP_SCHED_CONST = 2
@@ -57,6 +60,8 @@ class LpOptions(ctypes.Structure):
         ("kernel_timing", c_int32),
         ("device", c_int32),
         ("stream", c_void_p),
+        ("precision", c_int32),
+        ("refine_tol", c_double),
         ("reserved", c_int32 * 8),
     ]
 

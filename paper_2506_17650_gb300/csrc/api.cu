@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -19,7 +20,7 @@ using namespace lpop;
 
 namespace lpop {
 void launch_mul_into(double* out, const double* a, const double* f, int n, cudaStream_t s);
-int row_kernel_blocks_per_sm();
+void row_kernel_blocks_per_sm(int* primal, int* dual);
 }  // namespace lpop
 
 static thread_local std::string g_last_error;
@@ -46,7 +47,12 @@ struct lp_problem {
   long long host_attempts = 0;
   long long launches = 0;
   std::string err;
-  cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec = nullptr;    // FP64 check period
+  cudaGraphExec_t gexec32 = nullptr;  // FP32 check period (mixed precision)
+  bool mixed = false;
+  bool fp32_phase = false;  // mixed precision before the hand-over to FP64
+  double best_kkt = INFINITY;
+  int stall = 0;
   std::vector<cudaEvent_t> events;  // 3 per timed sample: before primal, between, after dual
   int samples = 0;
   double kt_ms[2] = {0.0, 0.0};
@@ -57,6 +63,40 @@ struct lp_problem {
 };
 
 namespace {
+
+// Step-size schedule factors 1 - (t+1)^-0.3 and 1 + (t+1)^-0.6 of the adaptive
+// step (PDLP rule) for t < kStepTab, computed once per device with the host
+// libm pow and shared by every problem on that device.
+std::mutex g_tab_mutex;
+double* g_step_tab[64] = {nullptr};
+
+const double* step_table(int dev, cudaStream_t s, cudaError_t* err) {
+  std::lock_guard<std::mutex> lock(g_tab_mutex);
+  *err = cudaSuccess;
+  if (dev < 0 || dev >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  if (!g_step_tab[dev]) {
+    std::vector<double> h(2 * (size_t)kStepTab);
+    for (int t = 0; t < kStepTab; ++t) {
+      const double tp1 = (double)t + 1.0;
+      h[t] = 1.0 - std::pow(tp1, -0.3);
+      h[kStepTab + t] = 1.0 + std::pow(tp1, -0.6);
+    }
+    void* dptr = nullptr;
+    *err = cudaMalloc(&dptr, h.size() * sizeof(double));
+    if (*err != cudaSuccess) return nullptr;
+    *err = cudaMemcpyAsync(dptr, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (*err == cudaSuccess) *err = cudaStreamSynchronize(s);
+    if (*err != cudaSuccess) {
+      cudaFree(dptr);
+      return nullptr;
+    }
+    g_step_tab[dev] = static_cast<double*>(dptr);
+  }
+  return g_step_tab[dev];
+}
 
 int set_err(lp_problem* p, int code, const std::string& msg) {
   if (p) p->err = msg;
@@ -104,6 +144,8 @@ int check_options(const lp_options& o, std::string& msg) {
   if (o.check_every < 1) return msg = "check_every must be >= 1", 1;
   if (o.power_iters < 1) return msg = "power_iters must be >= 1", 1;
   if (!(o.plain_step_factor > 0.0)) return msg = "plain_step_factor must be > 0", 1;
+  if (o.precision != LP_PREC_FP64 && o.precision != LP_PREC_MIXED) return msg = "unknown precision", 1;
+  if (!(o.refine_tol >= 0.0)) return msg = "refine_tol must be >= 0", 1;
   for (int i = 0; i < 8; ++i)
     if (o.reserved[i] != 0) return msg = "reserved option fields must be zero", 1;
   return 0;
@@ -129,10 +171,15 @@ int init_state(lp_problem* p) {
   s0.omega = p->omega0;
   s0.tol = 1e-4;
   s0.k_prev = INFINITY;
+  refresh_derived(s0, p->prm.phi);
   CK(cudaMemcpyAsync(p->d.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, p->stream));
   launch_init_vectors(p->d, p->stream);
-  launch_spmv_binned(p->d.A, p->d.binsA, p->d.gridA, p->d.x[0], p->d.ax[0], p->stream);
+  launch_spmv_binned(p->d.A, p->d.binsA, p->d.gridA, p->d.f64.x[0], p->d.f64.ax[0], p->stream);
+  if (p->mixed) launch_demote_state(p->d, p->stream);
   CK(cudaGetLastError());
+  p->fp32_phase = p->mixed;
+  p->best_kkt = INFINITY;
+  p->stall = 0;
   CK(cudaStreamSynchronize(p->stream));
   p->initial_check_done = false;
   p->solved_once = false;
@@ -187,17 +234,17 @@ int preprocess(lp_problem* p) {
   CK(cudaGetLastError());
   int rc = LP_OK;
   // norms of the caller's b and c (still unscaled), then rescale the vectors
-  launch_norm2(d.b, m, red, s);
+  launch_norm2(d.f64.b, m, red, s);
   p->prm.b_norm = m > 0 ? read_scalar(p, red, &rc) : 0.0;
   TRY(rc);
-  launch_norm2(d.c, n, red, s);
+  launch_norm2(d.f64.c, n, red, s);
   p->prm.c_norm = read_scalar(p, red, &rc);
   TRY(rc);
   launch_scale_problem_vectors(d, s);
-  launch_norm2(d.b, m, red, s);
+  launch_norm2(d.f64.b, m, red, s);
   const double bn = m > 0 ? read_scalar(p, red, &rc) : 0.0;
   TRY(rc);
-  launch_norm2(d.c, n, red, s);
+  launch_norm2(d.f64.c, n, red, s);
   const double cn = read_scalar(p, red, &rc);
   TRY(rc);
   p->omega0 = (bn > 0.0 && cn > 0.0) ? cn / bn : 1.0;
@@ -212,8 +259,8 @@ int preprocess(lp_problem* p) {
     p->eta0 = p->amax > 0.0 ? 1.0 / p->amax : 1.0;
   } else {
     // ||A~||_2 by power iteration on A~^T A~ from the all-ones direction
-    double* v = d.q;       // [n]
-    double* t = d.ax_avg;  // [m]
+    double* v = d.f64.q;       // [n]
+    double* t = d.f64.ax_avg;  // [m]
     double* w = fc;        // [n]
     p->norm_est = 0.0;
     if (p->nnz > 0) {
@@ -231,8 +278,23 @@ int preprocess(lp_problem* p) {
     }
     p->eta0 = p->norm_est > 0.0 ? p->opt.plain_step_factor / p->norm_est : 1.0;
   }
+  if (p->mixed) launch_make_fp32(d, s);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(s));
+  return LP_OK;
+}
+
+template <class V>
+int alloc_vecs(lp_problem* p, Vecs<V>& v, int m, int n, bool values) {
+  if (values) {
+    TRY(dalloc(p, &v.Av, (size_t)p->d.nnz));
+    TRY(dalloc(p, &v.Atv, (size_t)p->d.nnz));
+  }
+  V** vm[] = {&v.b, &v.y[0], &v.y[1], &v.ax[0], &v.ax[1], &v.ybar[0], &v.ybar[1],
+              &v.S, &v.invS, &v.GS, &v.p, &v.y_last, &v.ax_avg};
+  for (V** q : vm) TRY(dalloc(p, q, m));
+  V** vn[] = {&v.c, &v.l, &v.u, &v.x[0], &v.x[1], &v.xbar[0], &v.xbar[1], &v.T, &v.invT, &v.GT, &v.q, &v.x_last};
+  for (V** q : vn) TRY(dalloc(p, q, n));
   return LP_OK;
 }
 
@@ -249,25 +311,32 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
   TRY(dalloc(p, &d.At_rp, n + 1));
   TRY(dalloc(p, &d.At_ci, nz));
   TRY(dalloc(p, &d.At_v, nz));
-  double** vecs_m[] = {&d.b, &d.dr, &d.y[0], &d.y[1], &d.ax[0], &d.ax[1], &d.ybar[0], &d.ybar[1],
-                       &d.S, &d.GS, &d.p, &d.y_last, &d.ax_avg};
-  for (double** v : vecs_m) TRY(dalloc(p, v, m));
-  double** vecs_n[] = {&d.c, &d.l, &d.u, &d.dc, &d.x[0], &d.x[1], &d.xbar[0], &d.xbar[1],
-                       &d.T, &d.GT, &d.q, &d.x_last};
-  for (double** v : vecs_n) TRY(dalloc(p, v, n));
+  d.nnz = nz;
+  d.f64.Av = d.A_v;
+  d.f64.Atv = d.At_v;
+  TRY(dalloc(p, &d.dr, m));
+  TRY(dalloc(p, &d.dc, n));
+  TRY(alloc_vecs(p, d.f64, m, n, false));
+  if (p->mixed) TRY(alloc_vecs(p, d.f32, m, n, true));
+  TRY(dalloc(p, &d.work2, (size_t)(m > n ? m : n) + 1));
   TRY(dalloc(p, &d.sense, m));
   TRY(dalloc(p, &d.work, (size_t)m + n + 2048));
   TRY(dalloc(p, &d.st, 1));
+  {
+    cudaError_t te = cudaSuccess;
+    d.step_tab = step_table(p->device, p->stream, &te);
+    if (!d.step_tab) return set_err(p, LP_ERR_CUDA, std::string("step-size table: ") + cudaGetErrorString(te));
+  }
 
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  int per_sm = row_kernel_blocks_per_sm();
-  if (per_sm < 1) per_sm = 1;
-  d.max_grid = sms * per_sm;
+  int per_sm_p = 1, per_sm_d = 1;
+  row_kernel_blocks_per_sm(&per_sm_p, &per_sm_d);
+  d.max_grid = sms * (per_sm_p > per_sm_d ? per_sm_p : per_sm_d);
   d.binsA = lay.binsA;
   d.binsAt = lay.binsAt;
-  d.gridA = d.binsA.nunits < d.max_grid ? d.binsA.nunits : d.max_grid;
-  d.gridAt = d.binsAt.nunits < d.max_grid ? d.binsAt.nunits : d.max_grid;
+  d.gridA = d.binsA.nunits < sms * per_sm_d ? d.binsA.nunits : sms * per_sm_d;
+  d.gridAt = d.binsAt.nunits < sms * per_sm_p ? d.binsAt.nunits : sms * per_sm_p;
   if (d.gridA < 1) d.gridA = 1;
   if (d.gridAt < 1) d.gridAt = 1;
   const int maxg = d.gridA > d.gridAt ? d.gridA : d.gridAt;
@@ -289,20 +358,20 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
   std::vector<double> tm(m), tn(n);
   std::vector<uint8_t> ts(m);
   for (int i = 0; i < m; ++i) tm[i] = b[lay.prow[i]];
-  if (m > 0) CK(cudaMemcpyAsync(d.b, tm.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  if (m > 0) CK(cudaMemcpyAsync(d.f64.b, tm.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
   for (int i = 0; i < m; ++i) {
     const char c0 = sense[lay.prow[i]];
     ts[i] = c0 == 'E' ? kEq : (c0 == 'L' ? kLe : kGe);
   }
   if (m > 0) CK(cudaMemcpyAsync(d.sense, ts.data(), m, cudaMemcpyHostToDevice, s));
   for (int j = 0; j < n; ++j) tn[j] = c[lay.pcol[j]];
-  CK(cudaMemcpyAsync(d.c, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d.f64.c, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));  // tn is reused below
   for (int j = 0; j < n; ++j) tn[j] = lb[lay.pcol[j]];
-  CK(cudaMemcpyAsync(d.l, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d.f64.l, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
   for (int j = 0; j < n; ++j) tn[j] = ub[lay.pcol[j]];
-  CK(cudaMemcpyAsync(d.u, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d.f64.u, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
   return LP_OK;
 }
@@ -317,8 +386,9 @@ int create_events(lp_problem* p) {
 
 bool sampled(const lp_problem* p, int a) { return p->opt.kernel_timing && (a % 8) == 0; }
 
-int capture_graph(lp_problem* p) {
-  if (p->gexec) return LP_OK;
+int capture_graph(lp_problem* p, bool fp32) {
+  cudaGraphExec_t* slot = fp32 ? &p->gexec32 : &p->gexec;
+  if (*slot) return LP_OK;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
   const int ce = p->opt.check_every;
@@ -326,18 +396,18 @@ int capture_graph(lp_problem* p) {
     const bool tm = sampled(p, a);
     const int sidx = a / 8;
     if (tm) cudaEventRecordWithFlags(p->events[3 * sidx], p->stream, cudaEventRecordExternal);
-    launch_primal(p->d, p->prm, p->stream);
+    launch_primal(p->d, p->prm, fp32, p->stream);
     if (tm) cudaEventRecordWithFlags(p->events[3 * sidx + 1], p->stream, cudaEventRecordExternal);
-    launch_dual(p->d, p->prm, p->stream);
+    launch_dual(p->d, p->prm, fp32, p->stream);
     if (tm) cudaEventRecordWithFlags(p->events[3 * sidx + 2], p->stream, cudaEventRecordExternal);
   }
-  launch_check(p->d, p->prm, 0, p->stream);
+  launch_check(p->d, p->prm, 0, fp32, p->stream);
   cudaError_t e = cudaStreamEndCapture(p->stream, &g);
   if (e != cudaSuccess) return set_err(p, LP_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&p->gexec, g, 0);
+  e = cudaGraphInstantiate(slot, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    p->gexec = nullptr;
+    *slot = nullptr;
     return set_err(p, LP_ERR_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
   }
   return LP_OK;
@@ -355,6 +425,16 @@ int collect_times(lp_problem* p) {
     p->kt_n[1] += 1;
   }
   return LP_OK;
+}
+
+int download_vec(lp_problem* p, const double* dsrc, const double* dscale, int len, const std::vector<int>& perm,
+                 double* out);
+
+// The current phase's copy of a vector as FP64 on the device (FP32 vectors are widened into work2).
+const double* phase_vec(lp_problem* p, const double* v64, const float* v32, int len) {
+  if (!p->fp32_phase) return v64;
+  launch_widen(p->d.work2, v32, len, p->stream);
+  return p->d.work2;
 }
 
 int download_vec(lp_problem* p, const double* dsrc, const double* dscale, int len, const std::vector<int>& perm,
@@ -384,7 +464,7 @@ int upload_vec(lp_problem* p, double* ddst, const double* host, int len, const s
 
 int get_state_impl(lp_problem* p, double* vn, double* vm, double* scal) {
   TRY(select_device(p));
-  launch_flush_update(p->d, p->prm, p->stream);
+  launch_flush_update(p->d, p->prm, p->fp32_phase, p->stream);
   CK(cudaGetLastError());
   DevState hs;
   CK(cudaMemcpyAsync(&hs, p->d.st, sizeof(hs), cudaMemcpyDeviceToHost, p->stream));
@@ -392,12 +472,16 @@ int get_state_impl(lp_problem* p, double* vn, double* vm, double* scal) {
   const int n = p->d.n, m = p->d.m, c = hs.cur;
   const Dev& d = p->d;
   if (vn) {
-    const double* src[5] = {d.x[c], d.xbar[c], d.T, d.GT, d.x_last};
-    for (int k = 0; k < 5; ++k) TRY(download_vec(p, src[k], nullptr, n, p->pcol, vn + (size_t)k * n));
+    const double* s64[5] = {d.f64.x[c], d.f64.xbar[c], d.f64.T, d.f64.GT, d.f64.x_last};
+    const float* s32[5] = {d.f32.x[c], d.f32.xbar[c], d.f32.T, d.f32.GT, d.f32.x_last};
+    for (int k = 0; k < 5; ++k)
+      TRY(download_vec(p, phase_vec(p, s64[k], s32[k], n), nullptr, n, p->pcol, vn + (size_t)k * n));
   }
   if (vm) {
-    const double* src[6] = {d.y[c], d.ybar[c], d.ax[c], d.S, d.GS, d.y_last};
-    for (int k = 0; k < 6; ++k) TRY(download_vec(p, src[k], nullptr, m, p->prow, vm + (size_t)k * m));
+    const double* s64[6] = {d.f64.y[c], d.f64.ybar[c], d.f64.ax[c], d.f64.S, d.f64.GS, d.f64.y_last};
+    const float* s32[6] = {d.f32.y[c], d.f32.ybar[c], d.f32.ax[c], d.f32.S, d.f32.GS, d.f32.y_last};
+    for (int k = 0; k < 6; ++k)
+      TRY(download_vec(p, phase_vec(p, s64[k], s32[k], m), nullptr, m, p->prow, vm + (size_t)k * m));
   }
   if (scal) {
     const double v[16] = {hs.eta, hs.omega, hs.wsum, hs.gp_norm, hs.gd_norm, hs.klast_p2, hs.klast_d2,
@@ -417,9 +501,9 @@ int set_state_impl(lp_problem* p, const double* vn, const double* vm, const doub
   CK(cudaStreamSynchronize(p->stream));
   const int n = p->d.n, m = p->d.m, c = hs.cur;
   const Dev& d = p->d;
-  double* dn[5] = {d.x[c], d.xbar[c], d.T, d.GT, d.x_last};
+  double* dn[5] = {d.f64.x[c], d.f64.xbar[c], d.f64.T, d.f64.GT, d.f64.x_last};
   for (int k = 0; k < 5; ++k) TRY(upload_vec(p, dn[k], vn + (size_t)k * n, n, p->pcol));
-  double* dm[6] = {d.y[c], d.ybar[c], d.ax[c], d.S, d.GS, d.y_last};
+  double* dm[6] = {d.f64.y[c], d.f64.ybar[c], d.f64.ax[c], d.f64.S, d.f64.GS, d.f64.y_last};
   for (int k = 0; k < 6; ++k) TRY(upload_vec(p, dm[k], vm + (size_t)k * m, m, p->prow));
   hs.eta = scal[0];
   hs.omega = scal[1];
@@ -440,7 +524,11 @@ int set_state_impl(lp_problem* p, const double* vn, const double* vm, const doub
   hs.counter = 0;
   hs.restart_action = 0;
   hs.adopt_avg = 0;
+  refresh_derived(hs, p->prm.phi);
   CK(cudaMemcpyAsync(p->d.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, p->stream));
+  launch_inverse_preconditioners(p->d, false, p->stream);
+  if (p->fp32_phase) launch_demote_state(p->d, p->stream);  // the FP32 phase continues from the imported state
+  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->stream));
   p->host_attempts = hs.attempts;
   p->initial_check_done = scal[14] != 0.0;
@@ -453,6 +541,7 @@ void release(lp_problem* p) {
   cudaSetDevice(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->gexec32) cudaGraphExecDestroy(p->gexec32);
   for (auto e : p->events)
     if (e) cudaEventDestroy(e);
   for (void* v : p->allocs) cudaFree(v);
@@ -487,12 +576,15 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
       return set_err(nullptr, LP_ERR_INVALID_INPUT,
                      "bounds of variable " + std::to_string(j) + " are invalid (need lb <= ub, lb < inf, ub > -inf)");
   }
+  // FP64 rows take one lane up to 16 entries whatever the matrix size: extra
+  // lanes cost FP64 shuffle adds, which outweigh the added parallelism on GB300
   HostLayout lay;
-  int rc = build_layout(m, n, nnz, row_ptr, col_idx, val, lay, msg);
+  int rc = build_layout(m, n, nnz, row_ptr, col_idx, val, lay, msg, 0);
   if (rc != LP_OK) return set_err(nullptr, rc, msg);
 
   p = new lp_problem();
   p->opt = o;
+  p->mixed = o.precision == LP_PREC_MIXED;
   p->nnz = lay.nnz;
   auto fail = [&](int code) {
     g_last_error = p->err;
@@ -541,6 +633,36 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
   return LP_OK;
 }
 
+// Relative KKT error (max of the three ratios) of the last check's point.
+int read_kkt(lp_problem* p, double* kkt) {
+  CK(cudaMemcpyAsync(p->h_scratch, &p->d.st->pobj, 5 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  const double* v = p->h_scratch;  // pobj, dobj, rel_pres, rel_dres, rel_gap
+  *kkt = std::fmax(v[2], std::fmax(v[3], v[4]));
+  return LP_OK;
+}
+
+// Mixed precision: after a check in the FP32 phase, hand over to FP64 once the
+// relative KKT error is at most refine_tol or after 3 checks without a 10% gain.
+int maybe_refine(lp_problem* p) {
+  if (!p->fp32_phase) return LP_OK;
+  double kkt = 0.0;
+  TRY(read_kkt(p, &kkt));
+  if (kkt < 0.9 * p->best_kkt) {
+    p->best_kkt = kkt;
+    p->stall = 0;
+  } else {
+    p->stall += 1;
+  }
+  if (kkt <= p->opt.refine_tol || p->stall >= 3 || !std::isfinite(kkt)) {
+    launch_promote_state(p->d, p->stream);
+    CK(cudaGetLastError());
+    p->launches += 2;
+    p->fp32_phase = false;
+  }
+  return LP_OK;
+}
+
 int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_out) {
   TRY(select_device(p));
   const auto t0 = std::chrono::steady_clock::now();
@@ -552,7 +674,7 @@ int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_ou
   CK(cudaMemcpyAsync(&p->d.st->status, p->h_status, sizeof(int), cudaMemcpyHostToDevice, p->stream));
   int status = 0;
   if (!p->initial_check_done) {
-    launch_check(p->d, p->prm, 0, p->stream);
+    launch_check(p->d, p->prm, 0, p->fp32_phase, p->stream);
     CK(cudaGetLastError());
     p->launches += check_kernel_count();
     p->initial_check_done = true;
@@ -560,31 +682,36 @@ int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_ou
   }
   int out_status = LP_STATUS_NONE;
   while (status == 0 && p->host_attempts < iter_limit) {
+    const bool fp32 = p->fp32_phase;
     const long long to_boundary = ce - p->host_attempts % ce;
     const long long remaining = iter_limit - p->host_attempts;
+    bool checked = false;
     if (p->opt.use_graph && to_boundary == ce && remaining >= ce) {
-      TRY(capture_graph(p));
-      CK(cudaGraphLaunch(p->gexec, p->stream));
+      TRY(capture_graph(p, fp32));
+      CK(cudaGraphLaunch(fp32 ? p->gexec32 : p->gexec, p->stream));
       p->launches += 2LL * ce + check_kernel_count();
       p->host_attempts += ce;
+      checked = true;
       TRY(read_status(p, &status));
       TRY(collect_times(p));
     } else {
       const long long nrun = to_boundary < remaining ? to_boundary : remaining;
       for (long long a = 0; a < nrun; ++a) {
-        launch_primal(p->d, p->prm, p->stream);
-        launch_dual(p->d, p->prm, p->stream);
+        launch_primal(p->d, p->prm, fp32, p->stream);
+        launch_dual(p->d, p->prm, fp32, p->stream);
       }
       CK(cudaGetLastError());
       p->launches += 2 * nrun;
       p->host_attempts += nrun;
       if (p->host_attempts % ce == 0) {
-        launch_check(p->d, p->prm, 0, p->stream);
+        launch_check(p->d, p->prm, 0, fp32, p->stream);
         CK(cudaGetLastError());
         p->launches += check_kernel_count();
+        checked = true;
       }
       TRY(read_status(p, &status));
     }
+    if (status == 0 && checked) TRY(maybe_refine(p));
     if (p->opt.time_limit > 0.0) {
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (status == 0 && el > p->opt.time_limit) {
@@ -597,7 +724,7 @@ int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_ou
   else if (status == 4) out_status = LP_NUMERICAL_ERROR;
   else if (out_status == LP_STATUS_NONE) out_status = LP_ITERATION_LIMIT;
   if ((out_status == LP_ITERATION_LIMIT || out_status == LP_TIME_LIMIT) && p->host_attempts % ce != 0) {
-    launch_check(p->d, p->prm, 1, p->stream);
+    launch_check(p->d, p->prm, 1, p->fp32_phase, p->stream);
     CK(cudaGetLastError());
     p->launches += check_kernel_count();
   }
@@ -633,6 +760,8 @@ void lp_options_default(lp_options* o) {
   o->kernel_timing = 0;
   o->device = -1;
   o->stream = nullptr;
+  o->precision = LP_PREC_FP64;
+  o->refine_tol = 1e-6;
 }
 
 const char* lp_last_error(const lp_problem* p) {
@@ -668,8 +797,8 @@ int lp_result(lp_problem* p, double* x, double* y, lp_stats* st) {
   DevState hs;
   CK(cudaMemcpyAsync(&hs, p->d.st, sizeof(hs), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
-  TRY(download_vec(p, p->d.x[hs.cur], p->d.dc, p->d.n, p->pcol, x));
-  TRY(download_vec(p, p->d.y[hs.cur], p->d.dr, p->d.m, p->prow, y));
+  if (x) TRY(download_vec(p, phase_vec(p, p->d.f64.x[hs.cur], p->d.f32.x[hs.cur], p->d.n), p->d.dc, p->d.n, p->pcol, x));
+  if (y) TRY(download_vec(p, phase_vec(p, p->d.f64.y[hs.cur], p->d.f32.y[hs.cur], p->d.m), p->d.dr, p->d.m, p->prow, y));
   if (st) {
     std::memset(st, 0, sizeof(*st));
     st->pobj = hs.pobj;
@@ -691,15 +820,17 @@ int lp_result(lp_problem* p, double* x, double* y, lp_stats* st) {
 int lp_get_iterate(lp_problem* p, double* x, double* y, double* T, double* Sigma, double* scal) {
   if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
   TRY(select_device(p));
-  launch_flush_update(p->d, p->prm, p->stream);
+  launch_flush_update(p->d, p->prm, p->fp32_phase, p->stream);
   CK(cudaGetLastError());
   DevState hs;
   CK(cudaMemcpyAsync(&hs, p->d.st, sizeof(hs), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
-  TRY(download_vec(p, p->d.x[hs.cur], nullptr, p->d.n, p->pcol, x));
-  TRY(download_vec(p, p->d.y[hs.cur], nullptr, p->d.m, p->prow, y));
-  TRY(download_vec(p, p->d.T, nullptr, p->d.n, p->pcol, T));
-  TRY(download_vec(p, p->d.S, nullptr, p->d.m, p->prow, Sigma));
+  const Dev& d = p->d;
+  const int c = hs.cur;
+  if (x) TRY(download_vec(p, phase_vec(p, d.f64.x[c], d.f32.x[c], d.n), nullptr, d.n, p->pcol, x));
+  if (y) TRY(download_vec(p, phase_vec(p, d.f64.y[c], d.f32.y[c], d.m), nullptr, d.m, p->prow, y));
+  if (T) TRY(download_vec(p, phase_vec(p, d.f64.T, d.f32.T, d.n), nullptr, d.n, p->pcol, T));
+  if (Sigma) TRY(download_vec(p, phase_vec(p, d.f64.S, d.f32.S, d.m), nullptr, d.m, p->prow, Sigma));
   if (scal) {
     scal[0] = hs.eta;
     scal[1] = hs.omega;

@@ -15,10 +15,23 @@
 
 namespace lpop {
 
-struct Csr {
-  const int* rp;     // [rows+1]
-  const int* ci;     // [nnz]
-  const double* v;   // [nnz]
+template <class V>
+struct CsrT {
+  const int* rp;  // [rows+1]
+  const int* ci;  // [nnz]
+  const V* v;     // [nnz]
+};
+using Csr = CsrT<double>;
+
+// The per-iteration vectors and matrix values of one precision.  The FP64 set
+// always exists; the FP32 set only in mixed precision.  All in bin order.
+template <class V>
+struct Vecs {
+  V *Av, *Atv;  // values of A and A^T (same structure as the int arrays of Dev)
+  V *b, *c, *l, *u;
+  V *x[2], *y[2], *ax[2], *xbar[2], *ybar[2];
+  V *T, *invT, *S, *invS, *GT, *GS, *q, *p;
+  V *x_last, *y_last, *ax_avg;
 };
 
 // Options fixed for the life of a problem; passed by value to kernels.
@@ -71,34 +84,66 @@ struct DevState {
   double last_eta_max;
   // grid handshake counter for last-block reductions
   unsigned int counter;
+  // derived scalars, refreshed whenever eta, omega, k or the AdaGrad-norm sums change
+  int collect;        // the next attempt records q / p (k mod phi == 0)
+  double step_p;      // eta / omega
+  double step_d;      // eta * omega
+  double sqrt_gp;     // sqrt of gp_norm (0 when it is 0)
+  double sqrt_gd;
 };
+
+// Entries of the step-size schedule table (attempt counts below this use the table).
+constexpr int kStepTab = 1 << 20;
+
+// Refresh the derived scalars of a state (host and device).
+__host__ __device__ inline void refresh_derived(DevState& s, int phi) {
+  s.collect = phi > 0 && (s.k % phi) == 0;
+  s.step_p = s.eta / s.omega;
+  s.step_d = s.eta * s.omega;
+  s.sqrt_gp = s.gp_norm > 0.0 ? sqrt(s.gp_norm) : 0.0;
+  s.sqrt_gd = s.gd_norm > 0.0 ? sqrt(s.gd_norm) : 0.0;
+}
 
 // All device buffers of one problem.
 struct Dev {
   int m, n;
-  Csr A;    // m rows
-  Csr At;   // n rows
+  long long nnz;
+  Csr A;    // m rows, FP64 values
+  Csr At;   // n rows, FP64 values
   int *A_rp, *A_ci, *At_rp, *At_ci;
-  double *A_v, *At_v;
-  double *b, *c, *l, *u, *dr, *dc;  // preprocessed data, bin order
+  double *A_v, *At_v;  // == f64.Av, f64.Atv
+  double *dr, *dc;     // A~ = diag(dr) A diag(dc)
   uint8_t* sense;
-  double *x[2], *y[2], *ax[2], *xbar[2], *ybar[2];
-  double *T, *S, *GT, *GS, *q, *p;
-  double *x_last, *y_last, *ax_avg;
+  Vecs<double> f64;
+  Vecs<float> f32;    // null pointers unless mixed precision
   double* partials;   // [max_grid * kMaxPartials] written by primal/check-primal kernels
   double* partials2;  // same, written by dual/check-dual kernels
   double* work;       // small scratch for setup reductions
+  double* work2;      // [max(m, n)] FP64 staging of FP32 vectors read by the host
+  const double* step_tab;  // [2 * kStepTab]: 1 - (t+1)^-0.3 and 1 + (t+1)^-0.6 for t < kStepTab
   DevState* st;
   BinTable binsA, binsAt;
   int gridA, gridAt;  // blocks launched for the A / A^T row kernels
   int max_grid;
 };
 
+template <class V>
+__host__ __device__ inline const Vecs<V>& vecs(const Dev& d);
+template <>
+__host__ __device__ inline const Vecs<double>& vecs<double>(const Dev& d) { return d.f64; }
+template <>
+__host__ __device__ inline const Vecs<float>& vecs<float>(const Dev& d) { return d.f32; }
+
+template <class V>
+__host__ __device__ inline CsrT<V> csr_a(const Dev& d) { return CsrT<V>{d.A_rp, d.A_ci, vecs<V>(d).Av}; }
+template <class V>
+__host__ __device__ inline CsrT<V> csr_at(const Dev& d) { return CsrT<V>{d.At_rp, d.At_ci, vecs<V>(d).Atv}; }
+
 // ---------------------------------------------------------------------------
 // Block reductions (fixed shuffle tree then fixed smem order: deterministic)
 // ---------------------------------------------------------------------------
-template <int N>
-__device__ inline void block_sum(double (&v)[N], double* smem /* [32 * N] */) {
+template <int N, class T>
+__device__ inline void block_sum(T (&v)[N], T* smem /* [32 * N] */) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < N; ++q) {
@@ -115,7 +160,7 @@ __device__ inline void block_sum(double (&v)[N], double* smem /* [32 * N] */) {
   if (warp == 0) {
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      double t = lane < nw ? smem[lane * N + q] : 0.0;
+      T t = lane < nw ? smem[lane * N + q] : T(0);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
       v[q] = t;  // valid in warp 0
@@ -124,14 +169,73 @@ __device__ inline void block_sum(double (&v)[N], double* smem /* [32 * N] */) {
   __syncthreads();
 }
 
-// Sum `rows` partial records of width N (stride kMaxPartials) in a fixed order; result in thread 0.
+// Block sum through shared memory: every thread stores its N values, then one
+// warp adds them (8 per lane, then a shuffle tree).  Far fewer FP64
+// instructions than a shuffle tree in every warp.  Result valid in thread 0.
+// smem must hold N * blockDim.x doubles; blockDim.x must be 256.
+template <int N>
+__device__ inline void block_sum_smem(double (&v)[N], double* smem) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < N; ++q) smem[q * 256 + tid] = v[q];
+  __syncthreads();
+  if (tid < 32) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      double t = smem[q * 256 + tid];
+#pragma unroll
+      for (int k = 1; k < 8; ++k) t += smem[q * 256 + tid + 32 * k];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      v[q] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// Order-preserving integer key of a double (not NaN): comparisons of keys
+// agree with floating-point comparisons, and -0.0 and +0.0 get the same key.
+// Lets clamps and sign tests run on the integer pipes instead of the FP64 pipe.
+__device__ __forceinline__ long long ord_key(double v) {
+  const long long b = __double_as_longlong(v);
+  const long long mag = b & 0x7fffffffffffffffLL;
+  return b < 0 ? -mag : mag;
+}
+
+__device__ __forceinline__ int ord_key(float v) {
+  const int b = __float_as_int(v);
+  const int mag = b & 0x7fffffff;
+  return b < 0 ? -mag : mag;
+}
+
+// min(max(v, lo), hi) for lo <= hi, on the integer pipes.
+template <class V, class K>
+__device__ __forceinline__ V clamp_keys(V v, K kv, V lo, K kl, V hi, K kh) {
+  V r = kv < kl ? lo : v;
+  return kv > kh ? hi : r;
+}
+
+// Sum `rows` partial records of width N (stride kMaxPartials) in a fixed order;
+// result in thread 0.  Runs in one block on the critical path of every step,
+// so each thread first issues all of its loads (up to 4 records, independent)
+// and only then adds: one L2 round trip instead of one per record.
 template <int N>
 __device__ inline void sum_partials(const double* part, int rows, double (&out)[N], double* smem) {
 #pragma unroll
   for (int q = 0; q < N; ++q) out[q] = 0.0;
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+  for (int r0 = threadIdx.x; r0 < rows; r0 += 4 * blockDim.x) {
+    double v[4][N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) out[q] += __ldcg(part + (size_t)r * kMaxPartials + q);
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + u * blockDim.x;
+#pragma unroll
+      for (int q = 0; q < N; ++q) v[u][q] = r < rows ? __ldcg(part + (size_t)r * kMaxPartials + q) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) out[q] += v[u][q];
+    }
   }
   block_sum<N>(out, smem);
 }
@@ -158,12 +262,22 @@ __device__ inline bool publish_partials(double (&v)[N], double* part, unsigned i
 // Launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
 // one step attempt = primal kernel + dual kernel (the dual kernel's last block runs the step control)
-void launch_primal(const Dev& d, const Params& prm, cudaStream_t s);
-void launch_dual(const Dev& d, const Params& prm, cudaStream_t s);
+// fp32 selects the FP32 vector set (mixed precision); reductions and scalars stay FP64
+void launch_primal(const Dev& d, const Params& prm, bool fp32, cudaStream_t s);
+void launch_dual(const Dev& d, const Params& prm, bool fp32, cudaStream_t s);
 // KKT check: primal-side reductions, dual-side reductions + decision, apply
-void launch_check(const Dev& d, const Params& prm, int eval_only, cudaStream_t s);
+void launch_check(const Dev& d, const Params& prm, int eval_only, bool fp32, cudaStream_t s);
 // apply a pending preconditioner update now (debug reads)
-void launch_flush_update(const Dev& d, const Params& prm, cudaStream_t s);
+void launch_flush_update(const Dev& d, const Params& prm, bool fp32, cudaStream_t s);
+// recompute 1/T and 1/Sigma after T / Sigma were written from outside
+void launch_inverse_preconditioners(const Dev& d, bool fp32, cudaStream_t s);
+// mixed precision: FP32 copies of the problem data and the initial FP32 state
+void launch_make_fp32(const Dev& d, cudaStream_t s);
+// FP32 iterate -> FP64 iterate (refinement phase); FP64 -> FP32 (state import)
+void launch_promote_state(const Dev& d, cudaStream_t s);
+void launch_demote_state(const Dev& d, cudaStream_t s);
+// out[i] = (double) in[i] (reading FP32 vectors for the host)
+void launch_widen(double* out, const float* in, int n, cudaStream_t s);
 int check_kernel_count();
 
 // setup

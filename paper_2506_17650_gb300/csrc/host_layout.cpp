@@ -24,13 +24,22 @@ int bin_rank(int width) {
   }
 }
 
-constexpr long long kBlockRowThreshold = 1024;  // rows longer than this get a whole block
+constexpr long long kBlockRowThreshold = 2048;  // rows longer than this get a whole block
+
+// Power of two >= the ratio target / rows, capped at 8 (1 when rows fill the GPU).
+int widen_factor(long long rows, long long target_threads) {
+  int f = 1;
+  while (f < 8 && (long long)f * rows < target_threads) f <<= 1;
+  return f;
+}
 
 // Stable permutation of rows by bin rank.
-std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<int>& widths_sorted) {
+std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<int>& widths_sorted,
+                                 long long target_threads) {
   const int rows = (int)len.size();
+  const int widen = widen_factor(rows, target_threads);
   std::vector<int> width(rows);
-  for (int r = 0; r < rows; ++r) width[r] = width_for_length(len[r]);
+  for (int r = 0; r < rows; ++r) width[r] = width_for_length(len[r], widen);
   std::vector<int> perm(rows);
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return bin_rank(width[a]) < bin_rank(width[b]); });
@@ -41,14 +50,21 @@ std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<
 
 }  // namespace
 
-int width_for_length(long long len) {
-  if (len <= 2) return 1;
-  if (len <= 4) return 2;
-  if (len <= 8) return 4;
-  if (len <= 16) return 8;
-  if (len <= 32) return 16;
-  if (len <= kBlockRowThreshold) return 32;
-  return 0;
+// Lanes per row.  Short rows get one lane each: on GB300 the FP64 pipe, not
+// memory, limits these kernels, and one lane per row needs no shuffle adds to
+// combine lane sums.  Longer rows split over 4..32 lanes for coalescing.
+int width_for_length(long long len, int widen) {
+  int w;
+  if (len <= 16) w = 1;
+  else if (len <= 64) w = 4;
+  else if (len <= 256) w = 16;
+  else if (len <= kBlockRowThreshold) w = 32;
+  else return 0;
+  // a short row gains nothing from more lanes than entries
+  int cap = 1;
+  while (cap < len && cap < 32) cap <<= 1;
+  const int wide = widen < cap ? widen : cap;
+  return w > wide ? w : wide;
 }
 
 BinTable make_bins(const std::vector<int>& widths_sorted) {
@@ -74,7 +90,7 @@ BinTable make_bins(const std::vector<int>& widths_sorted) {
 }
 
 int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
-                 const double* val, HostLayout& out, std::string& err) {
+                 const double* val, HostLayout& out, std::string& err, long long target_threads) {
   if (m < 0 || n < 1 || nnz < 0) {
     err = "need m >= 0, n >= 1 and nnz >= 0";
     return LP_ERR_INVALID_ARG;
@@ -140,8 +156,8 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
   out.m = m;
   out.n = n;
   out.nnz = nz;
-  out.prow = bin_permutation(rlen, wA);
-  out.pcol = bin_permutation(clen, wAt);
+  out.prow = bin_permutation(rlen, wA, target_threads);
+  out.pcol = bin_permutation(clen, wAt, target_threads);
   out.binsA = make_bins(wA);
   out.binsAt = make_bins(wAt);
   std::vector<int> icol(n);

@@ -21,13 +21,17 @@ struct HostLayout {
   BinTable binsA{}, binsAt{};
 };
 
-// Lanes per row for a row of length len: 1, 2, 4, ..., 32, or 0 (a block per row).
-int width_for_length(long long len);
+// Lanes per row for a row of length len: 1, 2, 4, ..., 32, or 0 (a block per
+// row).  `widen` (a power of two >= 1) asks for up to that many lanes on short
+// rows when a matrix has too few rows to occupy the GPU with one lane each.
+int width_for_length(long long len, int widen = 1);
 
 // Validate the CSR input and build the layout.  Returns 0 on success, or a
-// negative lp_err code with a message in err.
+// negative lp_err code with a message in err.  target_threads: threads that
+// fill the GPU (SMs x resident threads); matrices with fewer rows get wider
+// row groups.
 int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
-                 const double* val, HostLayout& out, std::string& err);
+                 const double* val, HostLayout& out, std::string& err, long long target_threads = 0);
 
 // Bin table for rows already sorted by bin (widths non-increasing in "work" order).
 BinTable make_bins(const std::vector<int>& widths_sorted);

@@ -20,15 +20,19 @@ namespace lpop {
 
 namespace {
 
-template <int NV>
+// Vectors of type V (FP64, or FP32 in the mixed-precision phase); every
+// quantity of the check is formed and summed in FP64.
+template <int NV, class V>
 struct CheckPrimalOp {
-  const double *c, *l, *u, *dc, *xc, *xbarc, *xlast;
+  const V *c, *l, *u, *xc, *xbarc, *xlast;
+  const double* dc;
   double w;
   int avg;
   double acc[10];
+  __device__ __forceinline__ void prefetch(int) {}
 
   __device__ __forceinline__ void side(int j, double rc, double x, double* a) {
-    const double lo = __ldg(l + j), hi = __ldg(u + j);
+    const double lo = (double)__ldg(l + j), hi = (double)__ldg(u + j);
     const bool lf = isfinite(lo), uf = isfinite(hi);
     double lam;
     if (lf && uf) lam = rc;
@@ -40,28 +44,31 @@ struct CheckPrimalOp {
     a[0] += du * du;
     a[1] += ds * ds;
     a[2] += (lf ? lo * fmax(lam, 0.0) : 0.0) - (uf ? hi * fmax(-lam, 0.0) : 0.0);
-    a[3] += __ldg(c + j) * x;
-    const double dx = x - xlast[j];
+    a[3] += (double)__ldg(c + j) * x;
+    const double dx = x - (double)xlast[j];
     a[4] += dx * dx;
   }
 
   __device__ __forceinline__ void row(int j, const double (&s)[NV]) {
-    const double cj = __ldg(c + j);
-    side(j, cj - s[0], xc[j], acc);
-    if (NV > 1 && avg) side(j, cj - s[NV - 1] / w, xbarc[j] / w, acc + 5);
+    const double cj = (double)__ldg(c + j);
+    side(j, cj - s[0], (double)xc[j], acc);
+    if (NV > 1 && avg) side(j, cj - s[NV - 1] / w, (double)xbarc[j] / w, acc + 5);
   }
 };
 
+template <class V>
 struct CheckDualOp {
-  const double *b, *dr, *axc, *yc, *ybarc, *ylast;
+  const V *b, *axc, *yc, *ybarc, *ylast;
+  const double* dr;
   const uint8_t* sense;
-  double* ax_avg;
+  V* ax_avg;
   double w;
   int avg;
   double acc[8];
+  __device__ __forceinline__ void prefetch(int) {}
 
   __device__ __forceinline__ void side(int i, double ax, double y, double* a) {
-    const double bi = __ldg(b + i);
+    const double bi = (double)__ldg(b + i);
     const double rs = ax - bi;
     const uint8_t sn = __ldg(sense + i);
     const double ps = sn == kEq ? rs : (sn == kGe ? fmax(-rs, 0.0) : fmax(rs, 0.0));
@@ -69,38 +76,39 @@ struct CheckDualOp {
     a[0] += pu * pu;
     a[1] += ps * ps;
     a[2] += bi * y;
-    const double dy = y - ylast[i];
+    const double dy = y - (double)ylast[i];
     a[3] += dy * dy;
   }
 
   // s[0] = (A xbar)_i, used only when the average is a candidate
   __device__ __forceinline__ void row(int i, const double (&s)[1]) {
-    side(i, axc[i], yc[i], acc);
+    side(i, (double)axc[i], (double)yc[i], acc);
     if (avg) {
       const double axa = s[0] / w;
-      ax_avg[i] = axa;
-      side(i, axa, ybarc[i] / w, acc + 4);
+      ax_avg[i] = (V)axa;
+      side(i, axa, (double)ybarc[i] / w, acc + 4);
     }
   }
 };
 
-template <bool AVG>
+template <bool AVG, class V>
 __global__ void __launch_bounds__(kBlock) check_primal_kernel(Dev d) {
   __shared__ double smem[32 * kMaxPartials];
   constexpr int NV = AVG ? 2 : 1;
+  const Vecs<V>& v = vecs<V>(d);
   const DevState* st = d.st;
   const int cur = st->cur;
-  CheckPrimalOp<NV> op;
-  op.c = d.c; op.l = d.l; op.u = d.u; op.dc = d.dc;
-  op.xc = d.x[cur]; op.xbarc = d.xbar[cur]; op.xlast = d.x_last;
+  CheckPrimalOp<NV, V> op;
+  op.c = v.c; op.l = v.l; op.u = v.u; op.dc = d.dc;
+  op.xc = v.x[cur]; op.xbarc = v.xbar[cur]; op.xlast = v.x_last;
   op.w = st->wsum;
   op.avg = AVG && op.w > 0.0;
 #pragma unroll
   for (int q = 0; q < 10; ++q) op.acc[q] = 0.0;
-  Gather<NV> g;
-  g.x[0] = d.y[cur];
-  if (NV > 1) g.x[NV - 1] = d.ybar[cur];
-  for_each_row<NV>(d.binsAt, d.At, g, op, smem);
+  Gather<NV, V> g;
+  g.x[0] = v.y[cur];
+  if (NV > 1) g.x[NV - 1] = v.ybar[cur];
+  for_each_row<NV, V, double>(d.binsAt, csr_at<V>(d), g, op, smem);
   block_sum<10>(op.acc, smem);
   if (threadIdx.x == 0) {
     double* part = d.partials + (size_t)blockIdx.x * kMaxPartials;
@@ -121,9 +129,8 @@ __device__ __forceinline__ bool converged(const Cand& c, double tol) {
   return c.rel_p <= tol && c.rel_d <= tol && c.rel_g <= tol;
 }
 
-__device__ void check_control(const Dev& d, const Params& prm, const double (&p1)[10], const double (&p2)[8],
+__device__ void check_control(DevState* st, const Params& prm, const double (&p1)[10], const double (&p2)[8],
                               int eval_only, int avg_ok) {
-  DevState* st = d.st;
   Cand cd[2];
   for (int k = 0; k < 2; ++k) {
     Cand& c = cd[k];
@@ -198,25 +205,26 @@ __device__ void check_control(const Dev& d, const Params& prm, const double (&p1
   st->restarts += 1;
 }
 
-template <bool AVG>
+template <bool AVG, class V>
 __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, int eval_only) {
   __shared__ double smem[32 * kMaxPartials];
+  const Vecs<V>& v = vecs<V>(d);
   DevState* st = d.st;
   const int cur = st->cur;
   const double w = st->wsum;
   const int avg_ok = AVG && w > 0.0;
-  CheckDualOp op;
-  op.b = d.b; op.dr = d.dr; op.sense = d.sense;
-  op.axc = d.ax[cur]; op.yc = d.y[cur]; op.ybarc = d.ybar[cur]; op.ylast = d.y_last;
-  op.ax_avg = d.ax_avg;
+  CheckDualOp<V> op;
+  op.b = v.b; op.dr = d.dr; op.sense = d.sense;
+  op.axc = v.ax[cur]; op.yc = v.y[cur]; op.ybarc = v.ybar[cur]; op.ylast = v.y_last;
+  op.ax_avg = v.ax_avg;
   op.w = w;
   op.avg = avg_ok;
 #pragma unroll
   for (int q = 0; q < 8; ++q) op.acc[q] = 0.0;
   if (AVG) {
-    Gather<1> g;
-    g.x[0] = d.xbar[cur];
-    for_each_row<1>(d.binsA, d.A, g, op, smem);
+    Gather<1, V> g;
+    g.x[0] = v.xbar[cur];
+    for_each_row<1, V, double>(d.binsA, csr_a<V>(d), g, op, smem);
   } else {
     // without an average candidate only the cached A x is needed: no sparse product
     const double s0[1] = {0.0};
@@ -229,12 +237,17 @@ __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, i
   sum_partials<10>(d.partials, d.gridAt, p1, smem);
   sum_partials<8>(d.partials2, d.gridA, p2, smem);
   if (threadIdx.x == 0) {
-    check_control(d, prm, p1, p2, eval_only, avg_ok);
-    st->counter = 0;
+    DevState s = *st;  // register copy, written back once
+    check_control(&s, prm, p1, p2, eval_only, avg_ok);
+    refresh_derived(s, prm.phi);  // omega may have changed at a restart
+    s.counter = 0;
+    *st = s;
   }
 }
 
+template <class V>
 __global__ void check_apply_kernel(Dev d) {
+  const Vecs<V>& v = vecs<V>(d);
   const DevState* st = d.st;
   const int action = st->restart_action;
   const int adopt = st->adopt_avg;
@@ -245,25 +258,25 @@ __global__ void check_apply_kernel(Dev d) {
   const bool mark = action >= 1;
   const bool reset = action == 1 || action == 2;
   const int stride = gridDim.x * blockDim.x;
-  double *x = d.x[cur], *xb = d.xbar[cur], *y = d.y[cur], *yb = d.ybar[cur], *ax = d.ax[cur];
+  V *x = v.x[cur], *xb = v.xbar[cur], *y = v.y[cur], *yb = v.ybar[cur], *ax = v.ax[cur];
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
-    double v = x[j];
+    V val = x[j];
     if (to_avg) {
-      v = xb[j] / w;
-      x[j] = v;
+      val = (V)((double)xb[j] / w);
+      x[j] = val;
     }
-    if (mark) d.x_last[j] = v;
-    if (reset) xb[j] = 0.0;
+    if (mark) v.x_last[j] = val;
+    if (reset) xb[j] = V(0);
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) {
-    double v = y[i];
+    V val = y[i];
     if (to_avg) {
-      v = yb[i] / w;
-      y[i] = v;
-      ax[i] = d.ax_avg[i];
+      val = (V)((double)yb[i] / w);
+      y[i] = val;
+      ax[i] = v.ax_avg[i];
     }
-    if (mark) d.y_last[i] = v;
-    if (reset) yb[i] = 0.0;
+    if (mark) v.y_last[i] = val;
+    if (reset) yb[i] = V(0);
   }
 }
 
@@ -271,20 +284,26 @@ __global__ void check_apply_kernel(Dev d) {
 
 int check_kernel_count() { return 3; }
 
-void launch_check(const Dev& d, const Params& prm, int eval_only, cudaStream_t s) {
+template <class V>
+void launch_check_t(const Dev& d, const Params& prm, int eval_only, cudaStream_t s) {
   const bool avg = prm.mode == kPdlp && !eval_only;
   if (avg) {
-    check_primal_kernel<true><<<d.gridAt, kBlock, 0, s>>>(d);
-    check_dual_kernel<true><<<d.gridA, kBlock, 0, s>>>(d, prm, eval_only);
+    check_primal_kernel<true, V><<<d.gridAt, kBlock, 0, s>>>(d);
+    check_dual_kernel<true, V><<<d.gridA, kBlock, 0, s>>>(d, prm, eval_only);
   } else {
-    check_primal_kernel<false><<<d.gridAt, kBlock, 0, s>>>(d);
-    check_dual_kernel<false><<<d.gridA, kBlock, 0, s>>>(d, prm, eval_only);
+    check_primal_kernel<false, V><<<d.gridAt, kBlock, 0, s>>>(d);
+    check_dual_kernel<false, V><<<d.gridA, kBlock, 0, s>>>(d, prm, eval_only);
   }
   const int rows = d.n > d.m ? d.n : d.m;
   int grid = (rows + kBlock - 1) / kBlock;
   if (grid > 4 * 152) grid = 4 * 152;
   if (grid < 1) grid = 1;
-  check_apply_kernel<<<grid, kBlock, 0, s>>>(d);
+  check_apply_kernel<V><<<grid, kBlock, 0, s>>>(d);
+}
+
+void launch_check(const Dev& d, const Params& prm, int eval_only, bool fp32, cudaStream_t s) {
+  if (fp32) launch_check_t<float>(d, prm, eval_only, s);
+  else launch_check_t<double>(d, prm, eval_only, s);
 }
 
 }  // namespace lpop

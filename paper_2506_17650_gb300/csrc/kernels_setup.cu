@@ -78,13 +78,14 @@ __global__ void mul_kernel(double* a, const double* f, int n) {
 }
 
 __global__ void scale_vectors_kernel(Dev d) {
+  const Vecs<double>& v = d.f64;
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) d.b[i] = d.dr[i] * d.b[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) v.b[i] = d.dr[i] * v.b[i];
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
     const double f = d.dc[j];
-    d.c[j] = f * d.c[j];
-    d.l[j] = d.l[j] / f;
-    d.u[j] = d.u[j] / f;
+    v.c[j] = f * v.c[j];
+    v.l[j] = v.l[j] / f;
+    v.u[j] = v.u[j] / f;
   }
 }
 
@@ -140,33 +141,99 @@ __global__ void scale_by_inv_kernel(double* v, int n, const double* denom) {
 
 struct StoreOp {
   double* y;
+  __device__ __forceinline__ void prefetch(int) {}
   __device__ __forceinline__ void row(int r, const double (&s)[1]) { y[r] = s[0]; }
 };
 
 __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr M, BinTable bt, const double* x, double* y) {
   __shared__ double smem[32];
   StoreOp op{y};
-  Gather<1> g;
+  Gather<1, double> g;
   g.x[0] = x;
-  for_each_row<1>(bt, M, g, op, smem);
+  for_each_row<1, double, double>(bt, M, g, op, smem);
 }
 
 __global__ void init_vectors_kernel(Dev d) {
+  const Vecs<double>& v = d.f64;
   const int stride = gridDim.x * blockDim.x;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
-    const double x0 = fmin(fmax(0.0, d.l[j]), d.u[j]);
-    d.x[0][j] = x0; d.x[1][j] = x0;
-    d.xbar[0][j] = 0.0; d.xbar[1][j] = 0.0;
-    d.T[j] = 1.0; d.GT[j] = 0.0; d.q[j] = 0.0;
-    d.x_last[j] = x0;
+    const double x0 = fmin(fmax(0.0, v.l[j]), v.u[j]);
+    v.x[0][j] = x0; v.x[1][j] = x0;
+    v.xbar[0][j] = 0.0; v.xbar[1][j] = 0.0;
+    v.T[j] = 1.0; v.invT[j] = 1.0; v.GT[j] = 0.0; v.q[j] = 0.0;
+    v.x_last[j] = x0;
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) {
-    d.y[0][i] = 0.0; d.y[1][i] = 0.0;
-    d.ybar[0][i] = 0.0; d.ybar[1][i] = 0.0;
-    d.S[i] = 1.0; d.GS[i] = 0.0; d.p[i] = 0.0;
-    d.y_last[i] = 0.0;
-    d.ax_avg[i] = 0.0;
+    v.y[0][i] = 0.0; v.y[1][i] = 0.0;
+    v.ybar[0][i] = 0.0; v.ybar[1][i] = 0.0;
+    v.S[i] = 1.0; v.invS[i] = 1.0; v.GS[i] = 0.0; v.p[i] = 0.0;
+    v.y_last[i] = 0.0;
+    v.ax_avg[i] = 0.0;
   }
+}
+
+// FP32 copies of the preprocessed matrix values and problem vectors.
+__global__ void make_fp32_kernel(Dev d, long long nnz) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz; k += stride) {
+    d.f32.Av[k] = (float)d.f64.Av[k];
+    d.f32.Atv[k] = (float)d.f64.Atv[k];
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.m; i += stride) d.f32.b[i] = (float)d.f64.b[i];
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < d.n; j += stride) {
+    d.f32.c[j] = (float)d.f64.c[j];
+    d.f32.l[j] = (float)d.f64.l[j];
+    d.f32.u[j] = (float)d.f64.u[j];
+  }
+}
+
+// Copy the iteration state between the precisions: `up` = FP32 -> FP64
+// (start of the refinement phase), else FP64 -> FP32.  Only the current half
+// of the double buffers carries state; the other half is rewritten before use.
+template <class S, class D>
+__global__ void convert_state_kernel(Dev d, Vecs<S> src, Vecs<D> dst) {
+  const int cur = d.st->cur;
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
+    dst.x[cur][j] = (D)src.x[cur][j];
+    dst.xbar[cur][j] = (D)src.xbar[cur][j];
+    dst.T[j] = (D)src.T[j];
+    dst.invT[j] = D(1) / dst.T[j];
+    dst.GT[j] = (D)src.GT[j];
+    dst.q[j] = (D)src.q[j];
+    dst.x_last[j] = (D)src.x_last[j];
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) {
+    dst.y[cur][i] = (D)src.y[cur][i];
+    dst.ybar[cur][i] = (D)src.ybar[cur][i];
+    dst.ax[cur][i] = (D)src.ax[cur][i];
+    dst.S[i] = (D)src.S[i];
+    dst.invS[i] = D(1) / dst.S[i];
+    dst.GS[i] = (D)src.GS[i];
+    dst.p[i] = (D)src.p[i];
+    dst.y_last[i] = (D)src.y_last[i];
+    dst.ax_avg[i] = (D)src.ax_avg[i];
+  }
+}
+
+// A x of the current iterate, recomputed in FP64 after a promotion.
+struct StoreCurOp {
+  double* y;
+  __device__ __forceinline__ void prefetch(int) {}
+  __device__ __forceinline__ void row(int r, const double (&s)[1]) { y[r] = s[0]; }
+};
+
+__global__ void __launch_bounds__(kBlock) recompute_ax_kernel(Dev d) {
+  __shared__ double smem[32];
+  const int cur = d.st->cur;
+  StoreCurOp op{d.f64.ax[cur]};
+  Gather<1, double> g;
+  g.x[0] = d.f64.x[cur];
+  for_each_row<1, double, double>(d.binsA, d.A, g, op, smem);
+}
+
+__global__ void widen_kernel(double* out, const float* in, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (double)in[i];
 }
 
 int grid_for(long long n) {
@@ -183,7 +250,6 @@ int warp_grid_for(long long rows) {
   return (int)g;
 }
 
-// BinTable for a CSR matrix used only by spmv_kernel when no table is at hand
 }  // namespace
 
 void launch_fill(double* v, double val, long long n, cudaStream_t s) {
@@ -238,6 +304,29 @@ void launch_spmv_binned(const Csr& M, const BinTable& bt, int grid, const double
 
 void launch_init_vectors(const Dev& d, cudaStream_t s) {
   init_vectors_kernel<<<grid_for(d.n > d.m ? d.n : d.m), kBlock, 0, s>>>(d);
+}
+
+}  // namespace lpop
+
+namespace lpop {
+
+void launch_make_fp32(const Dev& d, cudaStream_t s) {
+  long long big = d.nnz > d.n ? d.nnz : d.n;
+  if (d.m > big) big = d.m;
+  make_fp32_kernel<<<grid_for(big), kBlock, 0, s>>>(d, d.nnz);
+}
+
+void launch_promote_state(const Dev& d, cudaStream_t s) {
+  convert_state_kernel<float, double><<<grid_for(d.n > d.m ? d.n : d.m), kBlock, 0, s>>>(d, d.f32, d.f64);
+  if (d.binsA.nunits > 0) recompute_ax_kernel<<<d.gridA, kBlock, 0, s>>>(d);
+}
+
+void launch_demote_state(const Dev& d, cudaStream_t s) {
+  convert_state_kernel<double, float><<<grid_for(d.n > d.m ? d.n : d.m), kBlock, 0, s>>>(d, d.f64, d.f32);
+}
+
+void launch_widen(double* out, const float* in, int n, cudaStream_t s) {
+  if (n > 0) widen_kernel<<<grid_for(n), kBlock, 0, s>>>(out, in, n);
 }
 
 }  // namespace lpop

@@ -18,7 +18,10 @@ Floating point is FP64 on both sides.  The bars:
   relative; they come from step differences (eta_max = ||dz||^2 /
   (2 |dy^T A dx|)) whose relative rounding error exceeds the iterates' by
   about ||z|| / ||dz||.
-* Full solves: same status; iteration count at 1e-4 within +-2%; final
+* Full solves: same status; iteration count at 1e-4 within +-2% of the range
+  the oracle itself spans under 1e-15 relative perturbations of c (the count
+  is rounding-sensitive in pdlp mode; where that range is one value this is
+  plain +-2%); final
   objective within 1e-6 relative when both sides solve to 1e-8 (at 1e-4 the
   objective itself is only determined to about the tolerance).
 """
@@ -145,10 +148,13 @@ def to_lib_state(S):
 
 
 def compare_full_state(g, S, where, rel_vec=1e-12, rel_scal=1e-10, prev=None):
-    """Compare the library's state after one step with the oracle's.  The next
-    step size is skipped when the step itself is at rounding level (relative
-    movement below 1e-9): eta_max = ||dz||^2 / (2 |dy^T A dx|) is then formed
-    from rounding noise on both sides."""
+    """Compare the library's state after one step with the oracle's.
+
+    The next step size comes from eta_max = ||dz||^2 / (2 |dy^T A dx|), formed
+    from the step dz itself, so its relative rounding error is about
+    eps ||z|| / ||dz||: it is compared at max(1e-10, 1e-13 ||z|| / ||dz||)
+    (1e-13 ~ 500 eps covers the sums), and skipped when the step is at
+    rounding level (||dz|| < 1e-9 ||z||)."""
     r = to_lib_state(S)
     keys = ["x", "xbar", "T", "GT", "y", "ybar", "ax", "Sigma", "GS"]
     if r["refs_set"]:
@@ -156,15 +162,17 @@ def compare_full_state(g, S, where, rel_vec=1e-12, rel_scal=1e-10, prev=None):
     for key in keys:
         ok, err = close(g[key], r[key], rel_vec)
         assert ok, f"{where}: {key} differs by {err:.3e} (norm {np.linalg.norm(r[key]):.3e})"
-    scalars = ["eta", "omega", "wsum", "gp_norm", "gd_norm"]
+    scalars = {"eta": rel_scal, "omega": rel_scal, "wsum": rel_scal, "gp_norm": rel_scal, "gd_norm": rel_scal}
     if prev is not None:
         move = np.linalg.norm(S.x - prev.x) + np.linalg.norm(S.y - prev.y)
         size = np.linalg.norm(S.x) + np.linalg.norm(S.y) + 1e-300
         if move < 1e-9 * size:
-            scalars.remove("eta")
-    for key in scalars:
-        ok, err = close([g[key]], [r[key]], rel_scal)
-        assert ok, f"{where}: {key} gpu {g[key]!r} oracle {r[key]!r}"
+            del scalars["eta"]
+        else:
+            scalars["eta"] = max(rel_scal, 1e-13 * size / move)
+    for key, tol in scalars.items():
+        ok, err = close([g[key]], [r[key]], tol)
+        assert ok, f"{where}: {key} gpu {g[key]!r} oracle {r[key]!r} (tolerance {tol:.1e})"
     for key in ("k", "attempts", "restarts", "refs_set", "last_restart_attempt"):
         assert g[key] == r[key], f"{where}: {key} gpu {g[key]} oracle {r[key]}"
 
@@ -219,6 +227,24 @@ def _as_trace(S):
                 wsum=S.wsum)
 
 
+def oracle_count_range(lp, o, tol, seeds=5, iter_limit=100_000):
+    """Iteration counts of the oracle to ``tol`` on the LP and on copies whose
+    cost vector is perturbed by 1e-15 relative (one per seed): the count the
+    method lands on is itself sensitive to rounding (on the transport LP these
+    perturbations move it between 576 and 1088), so a second correct FP64
+    implementation is held to this range widened by 2%."""
+    counts = []
+    for seed in range(seeds + 1):
+        P = oracle.scale_problem(lp, o)
+        if seed:
+            rng = np.random.default_rng(seed)
+            P.c = P.c * (1.0 + 1e-15 * rng.standard_normal(P.c.size))
+        S = oracle.initial_state(P, o)
+        r, _, _ = oracle.solve(lp, o, tol=tol, iter_limit=iter_limit, P=P, S=S)
+        counts.append(r.iterations)
+    return min(counts), max(counts)
+
+
 @pytest.mark.parametrize("case", ["tiny_plain_norm_freq", "tiny_pdlp_freq", "mixed_pdlp_adagrad",
                                   "rowmix_pdlp", "transport_small_pdlp"])
 def test_full_solve_matches_oracle(case):
@@ -233,8 +259,8 @@ def test_full_solve_matches_oracle(case):
         status_tight = p.solve(1e-8, 400_000)
         _, _, st_tight = p.result(want_x=False, want_y=False)
     assert status == res.status == lpop.LP_OPTIMAL
-    n_gpu, n_cpu = st["iterations"], res.iterations
-    assert abs(n_gpu - n_cpu) <= 0.02 * n_cpu, (n_gpu, n_cpu)
+    lo, hi = oracle_count_range(lp, o, 1e-4)
+    assert 0.98 * lo <= st["iterations"] <= 1.02 * hi, (st["iterations"], lo, hi, res.iterations)
     assert max(st["rel_pres"], st["rel_dres"], st["rel_gap"]) <= 1e-4
     assert status_tight == tight.status == lpop.LP_OPTIMAL
     assert st_tight["pobj"] == pytest.approx(tight.pobj, rel=1e-6, abs=1e-9)
@@ -254,7 +280,8 @@ def test_full_size_transport_solve():
         status = p.solve(1e-4, 20_000)
         _, _, st = p.result(want_x=False, want_y=False)
     assert status == res.status == lpop.LP_OPTIMAL
-    assert abs(st["iterations"] - res.iterations) <= 0.02 * res.iterations
+    lo, hi = oracle_count_range(lp, o, 1e-4, seeds=3)
+    assert 0.98 * lo <= st["iterations"] <= 1.02 * hi, (st["iterations"], lo, hi, res.iterations)
     # both points satisfy the 1e-4 relative KKT tolerance, which bounds their objectives' distance
     assert st["pobj"] == pytest.approx(res.pobj, rel=4e-4)
 
