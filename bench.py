@@ -32,31 +32,43 @@ TOL = 1e-4
 ALPHA = 1e-6  # from the paper's per-instance grid {1e-5, 1e-6, 1e-7} for the PDLP integration
 PHI = 20
 WORKLOAD = dict(n_supply=25_000, n_demand=25_000, n_arcs=200_000, seed=0)
+POWERLAW = dict(m=2_000_000, n=5_000_000, nnz=30_000_000, seed=0)
 L2_FLUSH_BYTES = 256 << 20
+# FP64 issue rate of GB300: 152 SMs x 2 FP64 lanes per cycle (an FMA counts once)
+SMS = 152
+FP64_LANES_PER_SM_CLK = 2
 
 
-def workload_name():
+def workload_name(kind="transport"):
+    if kind == "powerlaw":
+        w = POWERLAW
+        return (f"power-law LP: m={w['m']} (30% =, 70% <=), n={w['n']} (80% boxed, 20% free), ~{w['nnz']} nonzeros, "
+                f"column degrees power law (exponent 2.1), |a| log-uniform [1e-3, 1e3], seed {w['seed']}")
     w = WORKLOAD
     return (f"transport LP: m={w['n_supply'] + w['n_demand']} ({w['n_supply']} supply <=, {w['n_demand']} demand =), "
             f"n={w['n_arcs']} arcs, nnz={2 * w['n_arcs']}, costs U(1,100), x>=0, seed {w['seed']}")
 
 
-def make_lp():
+def make_lp(kind="transport", scale=1.0):
     import lpgen
 
+    if kind == "powerlaw":
+        w = POWERLAW
+        return lpgen.powerlaw(w["seed"], int(w["m"] * scale), int(w["n"] * scale), int(w["nnz"] * scale))
     w = WORKLOAD
     return lpgen.transport(w["seed"], w["n_supply"], w["n_demand"], w["n_arcs"])
 
 
-def base_config():
+def base_config(kind="transport"):
     return {
-        "workload": workload_name(),
+        "workload": workload_name(kind),
         "mode": "pdlp (adaptive step, primal weight, restarts)",
         "online": {"alpha": ALPHA, "phi": PHI, "normalize": True, "scheduler": "adagrad (diagonal)"},
         "tol": TOL,
         "step": "one full solve from the initial point to relative KKT 1e-4",
-        "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write); the 29 MB working set "
-              "stays L2-resident within a solve",
+        "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB write)"
+              + ("; the 29 MB working set stays L2-resident within a solve" if kind == "transport" else
+                 "; the working set (~2 GB) exceeds L2"),
     }
 
 
@@ -198,8 +210,58 @@ def kernel_bytes(m, n, nnz):
     return primal, dual
 
 
+def kernel_fp64_ops(m, n, nnz):
+    """FP64 operations per launch the method needs (an FMA counts once): one
+    FMA per nonzero of the product, and per row the step's arithmetic --
+    primal: g, T g, x - step T g, the average, dx, dx^2 / T (as dx^2 * (1/T))
+    and its sum (8); dual: r (2), Sigma r, y + step Sigma r, the average, dy,
+    dy^2 / Sigma and its sum, dy . A dx and its sum (10)."""
+    return nnz + 8 * n, nnz + 10 * m
+
+
+def aggregate_ranks(total_s, iters, world, device="cpu"):
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks."""
+    if world <= 1:
+        return total_s, iters
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([total_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
+def timed_solves(lpop, torch, prob, stream, flush, steps, warmup, tol, iter_limit):
+    """Reset, flush L2, then time one lp_solve with CUDA events on the library's
+    stream; repeat.  Returns per-step (ms, stats, status) and the summed kernel
+    timers and launch counts of the timed steps."""
+    out = []
+    kt_ms = [0.0, 0.0]
+    kt_n = [0, 0]
+    launches = 0
+    for i in range(warmup + steps):
+        prob.reset()
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            status = prob.solve(tol, iter_limit)
+            e1.record(stream)
+        e1.synchronize()
+        _, _, st = prob.result(want_x=False, want_y=False)
+        ms, ns, ln = prob.kernel_times()
+        if i >= warmup:
+            out.append((e0.elapsed_time(e1), st, status))
+            kt_ms = [kt_ms[0] + ms[0], kt_ms[1] + ms[1]]
+            kt_n = [kt_n[0] + int(ns[0]), kt_n[1] + int(ns[1])]
+            launches += ln
+    return out, kt_ms, kt_n, launches
+
+
 def gpu_arm(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -211,95 +273,83 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    kind = args.workload
+    large = kind == "powerlaw"
+    tol = 0.0 if large else TOL
+    iter_limit = 640 if large else 1_000_000
 
     # CPU baseline first (rank 0, N = 1 only), before the GPU work starts
-    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline and not large) else None
 
-    lp = make_lp()
+    lp = make_lp(kind, args.scale)
     stream = torch.cuda.Stream()
     opts = dict(alpha=ALPHA, phi=PHI, normalize=1, kernel_timing=1, device=local, stream=stream.cuda_stream)
     prob = lpop.Problem(lp, **opts)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     _, _, layout = prob.scaling()
 
-    def one_solve(timed):
-        prob.reset()
-        with torch.cuda.stream(stream):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            status = prob.solve(TOL, 1_000_000)
-            e1.record(stream)
-        e1.synchronize()
-        _, _, st = prob.result(want_x=False, want_y=False)
-        ms, ns, launches = prob.kernel_times()
-        return status, e0.elapsed_time(e1), st, ms, ns, launches
-
-    for _ in range(args.warmup):
-        one_solve(False)
+    timed_solves(lpop, torch, prob, stream, flush, 0, args.warmup, tol, iter_limit)
     clocks = Clocks(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    step_ms, iters, statuses, launches_total = [], 0, [], 0
-    kt_ms = np.zeros(2)
-    kt_n = np.zeros(2)
-    last = None
-    for _ in range(args.steps):
-        status, ms, st, kms, kns, launches = one_solve(True)
-        step_ms.append(ms)
-        iters += st["iterations"]
-        statuses.append(status)
-        kt_ms += kms
-        kt_n += kns
-        launches_total += launches
-        last = st
+    runs, kt_ms, kt_n, launches_total = timed_solves(lpop, torch, prob, stream, flush, args.steps, 0, tol,
+                                                     iter_limit)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
+    step_ms = [r[0] for r in runs]
+    iters = sum(r[1]["iterations"] for r in runs)
+    statuses = [r[2] for r in runs]
+    last = runs[-1][1]
 
     total_s = sum(step_ms) / 1e3
-    t_max = total_s
-    it_all = iters
-    if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        c = torch.tensor([float(iters)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        it_all = int(c.item())
+    t_max, it_all = aggregate_ranks(total_s, iters, world, device="cuda")
 
-    # fixed-preconditioner comparison (online update disabled) and end-to-end runs
-    fixed = None
-    e2e = None
+    fixed = mixed = e2e = None
     if rank == 0:
+        # the same solver with the online update disabled (fixed preconditioner)
         with lpop.Problem(lp, **dict(opts, alpha=0.0, kernel_timing=0)) as pf:
-            fms = []
-            for r in range(3):
-                pf.reset()
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                pf.solve(TOL, 1_000_000)
-                torch.cuda.synchronize()
-                fms.append(1e3 * (time.perf_counter() - t0))
-            _, _, fst = pf.result(want_x=False, want_y=False)
-        fixed = {"alpha": 0.0, "iterations": fst["iterations"], "time_to_tol_ms": statistics.median(fms),
-                 "pobj": fst["pobj"], "note": "same solver with the online update disabled"}
-        e2e = end_to_end(lpop, lp, opts, steps=3)
+            fr, _, _, _ = timed_solves(lpop, torch, pf, stream, flush, 3, 1, tol, iter_limit)
+        fixed = {"alpha": 0.0, "iterations": fr[-1][1]["iterations"],
+                 "time_to_tol_ms": None if large else statistics.median(r[0] for r in fr),
+                 "iters_per_s": sum(r[1]["iterations"] for r in fr) / (sum(r[0] for r in fr) / 1e3),
+                 "note": "same solver with the online update disabled"}
+        # mixed precision: FP32 products and updates, FP64 reductions and refinement
+        with lpop.Problem(lp, **dict(opts, precision=lpop.LP_PREC_MIXED)) as pm:
+            mr, mkt, mkn, _ = timed_solves(lpop, torch, pm, stream, flush, max(3, args.steps // 2), 1, tol,
+                                           iter_limit)
+        mst = mr[-1][1]
+        mixed = {"iters_per_s": sum(r[1]["iterations"] for r in mr) / (sum(r[0] for r in mr) / 1e3),
+                 "time_to_tol_ms": None if large else statistics.median(r[0] for r in mr),
+                 "iterations_per_solve": mst["iterations"],
+                 "status": "optimal" if all(r[2] == lpop.LP_OPTIMAL for r in mr) else str([r[2] for r in mr]),
+                 "rel_kkt": max(mst["rel_pres"], mst["rel_dres"], mst["rel_gap"]),
+                 "pobj": mst["pobj"],
+                 "primal_kernel_avg_us": 1e3 * mkt[0] / max(mkn[0], 1),
+                 "dual_kernel_avg_us": 1e3 * mkt[1] / max(mkn[1], 1),
+                 "dtype": "f32 products/updates, f64 reductions, f64 refinement",
+                 "accuracy": "KKT certified by the FP64 check; same tolerance as the FP64 path"}
+        if not large:
+            e2e = end_to_end(lpop, lp, opts, steps=3)
 
     m, n, nnz = lp.m, lp.n, lp.nnz
     pb, db = kernel_bytes(m, n, nnz)
+    pf64, df64 = kernel_fp64_ops(m, n, nnz)
     avg_primal_ms = kt_ms[0] / max(kt_n[0], 1)
     avg_dual_ms = kt_ms[1] / max(kt_n[1], 1)
     peak, peak_kind = measured_peaks()
     dom = "primal" if avg_primal_ms >= avg_dual_ms else "dual"
     dom_bytes = pb if dom == "primal" else db
+    dom_ops = pf64 if dom == "primal" else df64
     dom_ms = avg_primal_ms if dom == "primal" else avg_dual_ms
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
+    sm_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
+    fp64_peak = SMS * FP64_LANES_PER_SM_CLK * sm_clk / 1e9
+    fp64_achieved = dom_ops / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -314,19 +364,21 @@ def gpu_arm(args):
             "vs_baseline": None,
             "dtype": "f64",
             "data": "synthetic",
-            "config": base_config(),
-            "time_to_tol_ms": statistics.median(step_ms),
+            "config": dict(base_config(kind), **({"step": "640 step attempts from the initial point",
+                                                  "scale": args.scale} if large else {})),
+            "time_to_tol_ms": None if large else statistics.median(step_ms),
             "iterations_per_solve": last["iterations"],
-            "status": "optimal" if all(s == lpop.LP_OPTIMAL for s in statuses) else str(statuses),
+            "status": ("iteration limit (fixed-length steps)" if large else
+                       "optimal" if all(s_ == lpop.LP_OPTIMAL for s_ in statuses) else str(statuses)),
             "pobj": last["pobj"],
             "rel_kkt": max(last["rel_pres"], last["rel_dres"], last["rel_gap"]),
-            "solves_per_s": args.steps * world / t_max,
+            "solves_per_s": None if large else args.steps * world / t_max,
             "roofline": {
                 "bound": "hbm",
-                "kernel": f"{dom}_step_kernel (fused sparse product + update)",
+                "kernel": f"{dom}_step_kernel<double> (fused sparse product + update)",
                 "achieved": achieved,
                 "peak": peak,
-                "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth); the working set is L2-resident",
+                "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth)",
                 "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": None,
@@ -334,12 +386,17 @@ def gpu_arm(args):
                 "avg_launch_us": 1e3 * dom_ms,
                 "other_kernel_avg_us": 1e3 * (avg_dual_ms if dom == "primal" else avg_primal_ms),
                 "samples": int(kt_n[0]),
+                "fp64_alu": {"achieved": fp64_achieved, "peak": fp64_peak, "unit": "G FP64 inst/s",
+                             "frac": fp64_achieved / fp64_peak if fp64_achieved else None,
+                             "ops_per_launch": dom_ops,
+                             "peak_from": f"{SMS} SMs x {FP64_LANES_PER_SM_CLK} FP64 lanes/cycle x median SM clock"},
             },
             "gpu_launches": launches_total,
             "launch_layout": {k: layout[k] for k in ("grid_a", "grid_at", "units_a", "units_at")},
             "clocks": clk,
             "wall_s": wall,
             "fixed_precond": fixed,
+            "mixed_precision": mixed,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -347,6 +404,158 @@ def gpu_arm(args):
     prob.close()
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def sgm10(v):
+    import numpy as np
+
+    v = np.asarray(v, dtype=np.float64)
+    return float(np.exp(np.mean(np.log(v + 10.0))) - 10.0)
+
+
+def batch_arm(args):
+    """Many small LPs: 512 members (m log-uniform in [100, 20000], n = 2.5 m,
+    4-8 nonzeros per column, the tiny_random recipe per seed), mixed precision,
+    solved together by the batched kernel; autotuned team schedule against the
+    fixed one (one CTA per LP)."""
+    import numpy as np
+    import torch
+
+    import lpgen
+    import paper_2506_17650_gb300 as lpop
+    from paper_2506_17650_gb300 import build as lpbuild
+
+    lpbuild.build()
+    torch.cuda.set_device(0)
+    count = args.batch_count
+    ms, ns = lpgen.batch_sizes(0, count)
+    t0 = time.perf_counter()
+    lps = [lpgen.batch_member(10_000 + i, int(m), int(n)) for i, (m, n) in enumerate(zip(ms, ns))]
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    probs = [lpop.Problem(lp, alpha=ALPHA, phi=PHI, precision=lpop.LP_PREC_MIXED) for lp in lps]
+    create_s = time.perf_counter() - t0
+    nnz = np.array([lp.nnz for lp in lps])
+    out = {}
+    with lpop.Batch(probs) as b:
+        tuned = b.autotune(TOL, 128)
+        for name, sched in (("fixed", (1, 1 << 62)), ("autotuned", tuned[:2])):
+            b.set_schedule(*sched)
+            times = []
+            launches = 0
+            for rep in range(args.warmup + args.steps):
+                for p in probs:
+                    p.reset()
+                torch.cuda.synchronize()
+                l0 = b.launches()
+                t = time.perf_counter()
+                n_opt = b.solve(TOL, 200_000, 256)
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    times.append(time.perf_counter() - t)
+                    launches += b.launches() - l0
+            status, iters = b.status()
+            out[name] = {"schedule": {"cluster_size": int(sched[0]), "wide_nnz": int(min(sched[1], 1 << 62))},
+                         "solve_s": statistics.median(times), "solves_per_s": count / statistics.median(times),
+                         "optimal": int(n_opt), "iterations_sgm10": sgm10(iters),
+                         "iterations_median": float(np.median(iters)), "iterations_max": int(iters.max()),
+                         "iters_per_s": float(iters.sum()) / statistics.median(times),
+                         "gpu_launches": launches}
+    for p in probs:
+        p.close()
+    best = out["autotuned"]
+    line = {
+        "metric": METRIC, "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * best["solve_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 products/updates, f64 reductions and refinement", "data": "synthetic",
+        "config": {"workload": f"{count} LPs, m log-uniform [100, 20000], n = 2.5 m, 4-8 nonzeros per column, "
+                               f"sum nnz = {int(nnz.sum())}", "tol": TOL, "online": {"alpha": ALPHA, "phi": PHI},
+                   "step": "solve every member from its initial point to relative KKT 1e-4",
+                   "autotune_trial": {"cluster_size": tuned[0], "wide_nnz": int(min(tuned[1], 1 << 62)),
+                                      "trial_ms": tuned[2]}},
+        "batched": out, "generation_s": gen_s, "create_s": create_s, "gpu_launches": best["gpu_launches"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_arm(args):
+    """Poisson arrivals of power-law LPs (nnz log-uniform [1e3, max]); the
+    continuous-batching server against a one-LP-at-a-time FP64 loop on the
+    same request sequence."""
+    import numpy as np
+    import torch
+
+    import lpgen
+    import paper_2506_17650_gb300 as lpop
+    from paper_2506_17650_gb300 import build as lpbuild
+    from paper_2506_17650_gb300.serving import Server
+
+    lpbuild.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(0)
+    count = args.serve_count
+    nnzs = np.floor(10 ** rng.uniform(3, np.log10(args.serve_max_nnz), size=count)).astype(int)
+    lps = []
+    for i, z in enumerate(nnzs):
+        n = max(int(z / 6), 20)
+        m = max(int(0.4 * n), 8)
+        lps.append(lpgen.powerlaw(20_000 + i, m, n, int(z), dmax=max(m // 4, 4)))
+    # warm the library (first launches, graph capture paths)
+    with lpop.Problem(lps[0], alpha=ALPHA, phi=PHI) as p:
+        p.solve(TOL, 20_000)
+    # service time of the sequential FP64 loop sets the arrival rate: load ~ rate x mean service
+    seq_t = []
+    seq_lat = []
+    for lp in lps:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        with lpop.Problem(lp, alpha=ALPHA, phi=PHI) as p:
+            p.solve(TOL, 200_000)
+            p.result()
+        torch.cuda.synchronize()
+        seq_t.append(time.perf_counter() - t)
+    mean_service = float(np.mean(seq_t))
+    results = {}
+    for load in args.serve_loads:
+        rate = load / mean_service
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        # one at a time, FP64: a request waits for every earlier one
+        clock = 0.0
+        lat = []
+        for a, st in zip(arrivals, seq_t):
+            clock = max(clock, a) + st
+            lat.append(clock - a)
+        seq = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+               "solves_per_s": count / (clock - arrivals[0] + seq_t[0])}
+        srv = Server(tol=TOL, round_attempts=128, alpha=ALPHA, phi=PHI)
+        start = time.perf_counter()
+        srv.clock = lambda: time.perf_counter() - start
+        nxt = 0
+        while nxt < count or srv.active or srv.queue:
+            now = srv.clock()
+            while nxt < count and arrivals[nxt] <= now:
+                srv.submit(lps[nxt], arrival=float(arrivals[nxt]))
+                nxt += 1
+            if not srv.step() and nxt < count:
+                time.sleep(max(0.0, min(0.01, arrivals[nxt] - srv.clock())))
+        span = srv.clock() - arrivals[0]
+        rep = srv.latency_report()
+        srv.close()
+        results[f"load_{load}"] = {"arrival_rate_per_s": rate, "server": dict(rep, solves_per_s=count / span),
+                                   "one_at_a_time_fp64": seq}
+    line = {
+        "metric": METRIC, "value": results[f"load_{args.serve_loads[-1]}"]["server"]["solves_per_s"],
+        "unit": "solves/s", "n_gpus": 1, "steps": count, "warmup": 1, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 products/updates, f64 reductions and refinement",
+        "data": "synthetic",
+        "config": {"workload": f"{count} power-law LPs, nnz log-uniform [1e3, {args.serve_max_nnz:g}], n = nnz/6, "
+                               "m = 0.4 n, Poisson arrivals at load x (1 / mean FP64 service time)",
+                   "tol": TOL, "loads": list(args.serve_loads)},
+        "serving": results, "mean_fp64_service_s": mean_service,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -383,11 +592,21 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="transport", choices=["transport", "powerlaw", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serve-count", type=int, default=48)
+    ap.add_argument("--serve-max-nnz", type=float, default=1e6)
+    ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.5, 2.0])
+    ap.add_argument("--scale", type=float, default=1.0, help="size factor of the power-law workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch":
+        return batch_arm(args)
+    if args.workload == "serve":
+        return serve_arm(args)
     return gpu_arm(args)
 
 

@@ -252,6 +252,66 @@ int lp_power_norm_noalloc(int32_t m, int32_t n, const int32_t* a_row_ptr, const 
                           const double* a_val, const int32_t* at_row_ptr, const int32_t* at_col_idx,
                           const double* at_val, int32_t iters, void* stream, double* norm_out);
 
+/*
+ * Batched solves (many LPs advancing together in one persistent launch).
+ *
+ * A batch references existing problems (the members keep ownership of their
+ * data and state; destroy the batch before its members).  lp_batch_round runs
+ * every open member for up to `attempts` step attempts of Algorithm 1 with
+ * Eq. (6) -- checks, restarts and the online preconditioner updates included
+ * -- in ONE kernel launch.  Members with at least wide_nnz nonzeros are solved
+ * by a thread-block cluster of cluster_size CTAs, the others by one CTA each;
+ * members are assigned longest-first by nonzero count.  After each round the
+ * members' host views are refreshed, so lp_result / lp_get_state work on them
+ * as after lp_solve.  All members must live on one device; the batch uses the
+ * first member's stream.  Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
+ */
+typedef struct lp_batch lp_batch;
+
+int lp_batch_create(int32_t count, lp_problem* const* members, lp_batch** out);
+
+/* Replace the member list between rounds (serving: retire finished problems,
+ * admit new ones).  Members keep their state. */
+int lp_batch_set_members(lp_batch* b, int32_t count, lp_problem* const* members);
+
+/* Team schedule: cluster_size in {1, 2, 4, 8}; members with >= wide_nnz
+ * nonzeros get a whole cluster (default: cluster_size 1, no wide teams). */
+int lp_batch_set_schedule(lp_batch* b, int32_t cluster_size, int64_t wide_nnz);
+
+/* One round: every member with fewer than iter_limit attempts that is not yet
+ * finished under rel_kkt_tol runs up to `attempts` more (members finished
+ * under another tolerance are re-opened).  *active_out (may be NULL) receives
+ * the number of members still open afterwards. */
+int lp_batch_round(lp_batch* b, double rel_kkt_tol, int32_t attempts, int64_t iter_limit, int32_t* active_out);
+
+/* Rounds of round_attempts attempts until no member is open; *n_optimal (may
+ * be NULL) receives how many members reached the tolerance. */
+int lp_batch_solve(lp_batch* b, double rel_kkt_tol, int64_t iter_limit, int32_t round_attempts, int32_t* n_optimal);
+
+/* Schedule autotuner: for cluster sizes {1, 2, 4, 8} and wide thresholds at
+ * the 50/80/95/99th percentiles of the members' nonzero counts, reset every
+ * member (lp_reset), time one round of trial_attempts attempts with CUDA
+ * events, keep the fastest schedule, and reset the members again.  Outputs
+ * (may be NULL): the chosen cluster size and threshold, its trial time. */
+int lp_batch_autotune(lp_batch* b, double rel_kkt_tol, int32_t trial_attempts, int32_t* cluster_size,
+                      int64_t* wide_nnz, double* trial_ms);
+
+/* Per member (arrays of the batch's member count, either may be NULL): lp_status
+ * (0 while open) and step attempts so far. */
+int lp_batch_status(lp_batch* b, int32_t* status, int64_t* iterations);
+
+/* Kernel launches issued by the batch (rounds and state read-backs). */
+int lp_batch_launches(const lp_batch* b, int64_t* launches);
+
+/* Free the batch (not its members).  NULL is ignored. */
+void lp_batch_destroy(lp_batch* b);
+
+/* Device bytes lp_create allocates for a problem of this size with these
+ * options (after merging repeated entries nnz can only shrink), for callers
+ * that admit problems by free memory.  Writes *bytes; LP_ERR_INVALID_ARG on
+ * bad sizes or NULL bytes. */
+int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, int64_t* bytes);
+
 /* Free all device and host memory of the problem.  NULL is ignored. */
 void lp_destroy(lp_problem* p);
 

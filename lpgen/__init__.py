@@ -328,6 +328,48 @@ def row_length_mix(seed=0, lengths=(0, 1, 2, 3, 5, 8, 9, 16, 17, 31, 32, 33, 64,
     )
 
 
+def long_rows(seed=0, m=9000, n=12000, row_lengths=(4097, 8192, 11000), col_lengths=(4097, 6000, 8192),
+              background=(2, 4)):
+    """Sparse LP with a few rows of A and a few columns (rows of A^T) far longer
+    than the rest: the given lengths exactly, on a background of 2-4 nonzeros
+    per column.  For the products that cut very long rows into segments reduced
+    by several blocks (lengths just above, at and between segment multiples)."""
+    rng = np.random.default_rng(seed)
+    deg = rng.integers(background[0], background[1] + 1, size=n)
+    br, bc = _distinct_rows_per_column(rng, m, deg)
+    long_r = rng.choice(m, size=len(row_lengths), replace=False)
+    long_c = rng.choice(n, size=len(col_lengths), replace=False)
+    keys = [bc * m + br]
+    for r, L in zip(long_r, row_lengths):
+        keys.append(rng.choice(n, size=L, replace=False) * m + r)
+    for c, L in zip(long_c, col_lengths):
+        keys.append(c * m + rng.choice(m, size=L, replace=False))
+    key = np.unique(np.concatenate(keys))
+    rows, cols = key % m, key // m
+    # the long rows / columns hold exactly their lengths, except for entries
+    # shared with another long line or the background; trim those from the background
+    keep = np.ones(key.size, dtype=bool)
+    for r, L in zip(long_r, row_lengths):
+        idx = np.flatnonzero(rows == r)
+        extra = idx.size - L
+        if extra > 0:
+            bg = idx[~np.isin(cols[idx], long_c)]
+            keep[bg[:extra]] = False
+    for c, L in zip(long_c, col_lengths):
+        idx = np.flatnonzero((cols == c) & keep)
+        extra = idx.size - L
+        if extra > 0:
+            bg = idx[~np.isin(rows[idx], long_r)]
+            keep[bg[:extra]] = False
+    rows, cols = rows[keep], cols[keep]
+    vals = rng.standard_normal(rows.size)
+    return from_pattern(
+        m, n, rows, cols, vals, rng,
+        sense_probs=(0.4, 0.3, 0.3), var_probs=(0.6, 0.2, 0.2),
+        p_at_lower=0.3, p_at_upper=0.1, name=f"long_rows_m{m}_n{n}",
+    )
+
+
 def batch_sizes(seed=0, count=512, m_lo=100, m_hi=20_000):
     """Sizes m = floor(10^U(log10 m_lo, log10 m_hi)) for a batch of small LPs (n = 2.5 m)."""
     rng = np.random.default_rng(seed)

@@ -132,6 +132,27 @@ def load_library(path: str | None = None):
     lib.lp_power_norm_noalloc.argtypes = [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                           c_void_p, c_int32, c_void_p, POINTER(c_double)]
     lib.lp_power_norm_noalloc.restype = c_int32
+    lib.lp_batch_create.argtypes = [c_int32, POINTER(c_void_p), POINTER(c_void_p)]
+    lib.lp_batch_create.restype = c_int32
+    lib.lp_batch_set_members.argtypes = [c_void_p, c_int32, POINTER(c_void_p)]
+    lib.lp_batch_set_members.restype = c_int32
+    lib.lp_batch_set_schedule.argtypes = [c_void_p, c_int32, c_int64]
+    lib.lp_batch_set_schedule.restype = c_int32
+    lib.lp_batch_round.argtypes = [c_void_p, c_double, c_int32, c_int64, POINTER(c_int32)]
+    lib.lp_batch_round.restype = c_int32
+    lib.lp_batch_solve.argtypes = [c_void_p, c_double, c_int64, c_int32, POINTER(c_int32)]
+    lib.lp_batch_solve.restype = c_int32
+    lib.lp_batch_autotune.argtypes = [c_void_p, c_double, c_int32, POINTER(c_int32), POINTER(c_int64),
+                                      POINTER(c_double)]
+    lib.lp_batch_autotune.restype = c_int32
+    lib.lp_batch_status.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_int64)]
+    lib.lp_batch_status.restype = c_int32
+    lib.lp_batch_launches.argtypes = [c_void_p, POINTER(c_int64)]
+    lib.lp_batch_launches.restype = c_int32
+    lib.lp_batch_destroy.argtypes = [c_void_p]
+    lib.lp_batch_destroy.restype = None
+    lib.lp_memory_bytes.argtypes = [c_int32, c_int32, c_int64, POINTER(LpOptions), POINTER(c_int64)]
+    lib.lp_memory_bytes.restype = c_int32
     lib.lp_destroy.argtypes = [c_void_p]
     lib.lp_destroy.restype = None
     lib.lp_last_error.argtypes = [c_void_p]
@@ -281,6 +302,14 @@ def lp_power_norm_noalloc(m, n, a_row_ptr, a_col_idx, a_val, at_row_ptr, at_col_
     return out.value
 
 
+def lp_memory_bytes(m, n, nnz, opts: LpOptions | None = None) -> int:
+    """Device bytes lp_create allocates for a problem of this size (admission by free memory)."""
+    v = c_int64(0)
+    _check(load_library().lp_memory_bytes(int(m), int(n), int(nnz), ctypes.byref(opts) if opts is not None else None,
+                                          ctypes.byref(v)))
+    return v.value
+
+
 def lp_destroy(handle):
     if handle:
         load_library().lp_destroy(handle)
@@ -343,3 +372,108 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def _handles(problems):
+    arr = (c_void_p * max(len(problems), 1))()
+    for i, p in enumerate(problems):
+        arr[i] = p.handle if isinstance(p, Problem) else p
+    return arr
+
+
+def lp_batch_create(problems):
+    h = c_void_p()
+    _check(load_library().lp_batch_create(len(problems), _handles(problems), ctypes.byref(h)))
+    return h
+
+
+def lp_batch_set_members(batch, problems):
+    _check(load_library().lp_batch_set_members(batch, len(problems), _handles(problems)))
+
+
+def lp_batch_set_schedule(batch, cluster_size=1, wide_nnz=1 << 62):
+    _check(load_library().lp_batch_set_schedule(batch, int(cluster_size), int(wide_nnz)))
+
+
+def lp_batch_round(batch, rel_kkt_tol=1e-4, attempts=64, iter_limit=1_000_000) -> int:
+    act = c_int32(0)
+    _check(load_library().lp_batch_round(batch, float(rel_kkt_tol), int(attempts), int(iter_limit), ctypes.byref(act)))
+    return act.value
+
+
+def lp_batch_solve(batch, rel_kkt_tol=1e-4, iter_limit=1_000_000, round_attempts=256) -> int:
+    n = c_int32(0)
+    _check(load_library().lp_batch_solve(batch, float(rel_kkt_tol), int(iter_limit), int(round_attempts),
+                                         ctypes.byref(n)))
+    return n.value
+
+
+def lp_batch_autotune(batch, rel_kkt_tol=1e-4, trial_attempts=128):
+    """Pick the fastest team schedule on a trial round (resets every member); returns (cluster, wide_nnz, ms)."""
+    c = c_int32(0)
+    w = c_int64(0)
+    ms = c_double(0.0)
+    _check(load_library().lp_batch_autotune(batch, float(rel_kkt_tol), int(trial_attempts), ctypes.byref(c),
+                                            ctypes.byref(w), ctypes.byref(ms)))
+    return c.value, w.value, ms.value
+
+
+def lp_batch_status(batch, count):
+    st = np.zeros(count, dtype=np.int32)
+    it = np.zeros(count, dtype=np.int64)
+    _check(load_library().lp_batch_status(batch, st.ctypes.data_as(POINTER(c_int32)),
+                                          it.ctypes.data_as(POINTER(c_int64))))
+    return st, it
+
+
+def lp_batch_launches(batch) -> int:
+    v = c_int64(0)
+    _check(load_library().lp_batch_launches(batch, ctypes.byref(v)))
+    return v.value
+
+
+def lp_batch_destroy(batch):
+    if batch:
+        load_library().lp_batch_destroy(batch)
+
+
+class Batch:
+    """Owning wrapper of a batch over Problem objects (which stay owned by the caller)."""
+
+    def __init__(self, problems, cluster_size=1, wide_nnz=1 << 62):
+        self.problems = list(problems)
+        self.handle = lp_batch_create(self.problems)
+        lp_batch_set_schedule(self.handle, cluster_size, wide_nnz)
+
+    def set_members(self, problems):
+        self.problems = list(problems)
+        lp_batch_set_members(self.handle, self.problems)
+
+    def set_schedule(self, cluster_size, wide_nnz):
+        lp_batch_set_schedule(self.handle, cluster_size, wide_nnz)
+
+    def round(self, rel_kkt_tol=1e-4, attempts=64, iter_limit=1_000_000):
+        return lp_batch_round(self.handle, rel_kkt_tol, attempts, iter_limit)
+
+    def solve(self, rel_kkt_tol=1e-4, iter_limit=1_000_000, round_attempts=256):
+        return lp_batch_solve(self.handle, rel_kkt_tol, iter_limit, round_attempts)
+
+    def autotune(self, rel_kkt_tol=1e-4, trial_attempts=128):
+        return lp_batch_autotune(self.handle, rel_kkt_tol, trial_attempts)
+
+    def status(self):
+        return lp_batch_status(self.handle, len(self.problems))
+
+    def launches(self):
+        return lp_batch_launches(self.handle)
+
+    def close(self):
+        if self.handle:
+            lp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

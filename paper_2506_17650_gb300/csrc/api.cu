@@ -171,6 +171,8 @@ int init_state(lp_problem* p) {
   s0.omega = p->omega0;
   s0.tol = 1e-4;
   s0.k_prev = INFINITY;
+  s0.phase32 = p->mixed ? 1 : 0;
+  s0.best_kkt = INFINITY;
   refresh_derived(s0, p->prm.phi);
   CK(cudaMemcpyAsync(p->d.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, p->stream));
   launch_init_vectors(p->d, p->stream);
@@ -335,11 +337,30 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
   d.max_grid = sms * (per_sm_p > per_sm_d ? per_sm_p : per_sm_d);
   d.binsA = lay.binsA;
   d.binsAt = lay.binsAt;
-  d.gridA = d.binsA.nunits < sms * per_sm_d ? d.binsA.nunits : sms * per_sm_d;
-  d.gridAt = d.binsAt.nunits < sms * per_sm_p ? d.binsAt.nunits : sms * per_sm_p;
-  if (d.gridA < 1) d.gridA = 1;
-  if (d.gridAt < 1) d.gridAt = 1;
-  const int maxg = d.gridA > d.gridAt ? d.gridA : d.gridAt;
+  // grids from the unit counts; rows longer than half a block's share of the
+  // work are then cut into segments, which adds units
+  const int cap_d = sms * per_sm_d, cap_p = sms * per_sm_p;
+  auto grid_of = [](int units, int cap) { return units < 1 ? 1 : (units < cap ? units : cap); };
+  std::vector<int> segA = segment_long_rows(d.binsA, lay.A_rp, segment_length(nz, grid_of(d.binsA.nunits, cap_d)));
+  std::vector<int> segAt =
+      segment_long_rows(d.binsAt, lay.At_rp, segment_length(nz, grid_of(d.binsAt.nunits, cap_p)));
+  d.gridA = grid_of(d.binsA.nunits, cap_d);
+  d.gridAt = grid_of(d.binsAt.nunits, cap_p);
+  for (int which = 0; which < 2; ++which) {
+    BinTable& bt = which ? d.binsAt : d.binsA;
+    const std::vector<int>& units = which ? segAt : segA;
+    if (units.empty()) continue;
+    int* su = nullptr;
+    TRY(dalloc(p, &su, units.size()));
+    TRY(dalloc(p, &bt.seg_sum, units.size()));
+    TRY(dalloc(p, &bt.ticket, (size_t)bt.seg_rows));
+    CK(cudaMemcpyAsync(su, units.data(), sizeof(int) * units.size(), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemsetAsync(bt.ticket, 0, sizeof(unsigned int) * bt.seg_rows, p->stream));
+    bt.seg_unit = su;
+  }
+  CK(cudaStreamSynchronize(p->stream));
+  const int rows_a = partial_rows_a(d), rows_at = partial_rows_at(d);
+  const int maxg = rows_a > rows_at ? rows_a : rows_at;
   TRY(dalloc(p, &d.partials, (size_t)maxg * kMaxPartials));
   TRY(dalloc(p, &d.partials2, (size_t)maxg * kMaxPartials));
   d.A = Csr{d.A_rp, d.A_ci, d.A_v};
@@ -524,6 +545,8 @@ int set_state_impl(lp_problem* p, const double* vn, const double* vm, const doub
   hs.counter = 0;
   hs.restart_action = 0;
   hs.adopt_avg = 0;
+  hs.initial_checked = scal[14] != 0.0;
+  hs.phase32 = p->fp32_phase ? 1 : 0;
   refresh_derived(hs, p->prm.phi);
   CK(cudaMemcpyAsync(p->d.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, p->stream));
   launch_inverse_preconditioners(p->d, false, p->stream);
@@ -625,6 +648,7 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
   p->prm.check_every = o.check_every;
   p->prm.alpha = o.alpha;
   p->prm.floor = o.precond_floor;
+  p->prm.refine_tol = o.refine_tol;
   if ((rc = upload(p, lay, b, c, lb, ub, sense)) != LP_OK) return fail(rc);
   if ((rc = preprocess(p)) != LP_OK) return fail(rc);
   if ((rc = create_events(p)) != LP_OK) return fail(rc);
@@ -657,10 +681,30 @@ int maybe_refine(lp_problem* p) {
   if (kkt <= p->opt.refine_tol || p->stall >= 3 || !std::isfinite(kkt)) {
     launch_promote_state(p->d, p->stream);
     CK(cudaGetLastError());
+    *p->h_status = 0;
+    CK(cudaMemcpyAsync(&p->d.st->phase32, p->h_status, sizeof(int), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
     p->launches += 2;
     p->fp32_phase = false;
   }
   return LP_OK;
+}
+
+// A tolerance reached in the FP32 phase is measured against the FP32 copy of
+// A~; it ends the FP32 phase instead, and an FP64 termination test of the
+// promoted point decides.
+int certify_fp32(lp_problem* p, int* status) {
+  if (!p->fp32_phase || *status != 1) return LP_OK;
+  launch_promote_state(p->d, p->stream);
+  CK(cudaGetLastError());
+  p->h_status[0] = 0;
+  CK(cudaMemcpyAsync(&p->d.st->phase32, p->h_status, sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemcpyAsync(&p->d.st->status, p->h_status, sizeof(int), cudaMemcpyHostToDevice, p->stream));
+  p->fp32_phase = false;
+  launch_check(p->d, p->prm, 2, false, p->stream);
+  CK(cudaGetLastError());
+  p->launches += 2 + check_kernel_count();
+  return read_status(p, status);
 }
 
 int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_out) {
@@ -679,6 +723,7 @@ int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_ou
     p->launches += check_kernel_count();
     p->initial_check_done = true;
     TRY(read_status(p, &status));
+    TRY(certify_fp32(p, &status));
   }
   int out_status = LP_STATUS_NONE;
   while (status == 0 && p->host_attempts < iter_limit) {
@@ -711,6 +756,7 @@ int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_ou
       }
       TRY(read_status(p, &status));
     }
+    TRY(certify_fp32(p, &status));
     if (status == 0 && checked) TRY(maybe_refine(p));
     if (p->opt.time_limit > 0.0) {
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -737,6 +783,40 @@ int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_ou
 }
 
 }  // namespace
+
+namespace lpop {
+
+struct MemberView {
+  Dev d;
+  Params prm;
+  cudaStream_t stream;
+  int device;
+  bool mixed;
+};
+
+// Device layout of a problem, for the batched kernel.
+int member_view(lp_problem* p, MemberView* out) {
+  if (!p || !out) return LP_ERR_INVALID_ARG;
+  out->d = p->d;
+  out->prm = p->prm;
+  out->stream = p->stream;
+  out->device = p->device;
+  out->mixed = p->mixed;
+  return LP_OK;
+}
+
+// Host-side view of a problem after a batched kernel advanced its device state.
+int member_after_batch(lp_problem* p, const DevState& s) {
+  if (!p) return LP_ERR_INVALID_ARG;
+  p->host_attempts = s.attempts;
+  p->initial_check_done = s.initial_checked != 0;
+  p->fp32_phase = s.phase32 != 0;
+  p->solved_once = true;
+  p->last_status = s.status == 1 ? LP_OPTIMAL : (s.status == 4 ? LP_NUMERICAL_ERROR : LP_ITERATION_LIMIT);
+  return LP_OK;
+}
+
+}  // namespace lpop
 
 extern "C" {
 
@@ -885,6 +965,27 @@ int lp_reset(lp_problem* p) {
   if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
   TRY(select_device(p));
   return init_state(p);
+}
+
+int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, int64_t* bytes) {
+  if (!bytes || m < 0 || n < 1 || nnz < 0) return set_err(nullptr, LP_ERR_INVALID_ARG, "bad sizes or NULL bytes");
+  lp_options o;
+  if (opt) o = *opt;
+  else lp_options_default(&o);
+  // mirrors upload(): each cudaMalloc is rounded up to 256 bytes
+  auto r = [](long long b) { return ((b < 8 ? 8 : b) + 255) / 256 * 256; };
+  long long t = 0;
+  t += r(4LL * (m + 1)) + 2 * r(4LL * nnz) + 2 * r(8LL * nnz) + r(4LL * (n + 1));  // CSR of A and A^T
+  t += r(8LL * m) + r(8LL * n);                                                    // dr, dc
+  t += 13 * r(8LL * m) + 12 * r(8LL * n);                                          // FP64 vector set
+  if (o.precision == LP_PREC_MIXED) t += 2 * r(4LL * nnz) + 13 * r(4LL * m) + 12 * r(4LL * n);  // FP32 set
+  t += r(8LL * (m > n ? m : n) + 8) + r(m) + r(8LL * ((long long)m + n + 2048)) + r(sizeof(DevState));
+  // segmented rows (segments are at least 4096 entries): at most S rows and 2 S units per matrix
+  const long long S = nnz / 4096 + 1;
+  t += 2 * (r(8LL * 2 * S) + r(16LL * 2 * S) + r(4LL * S));
+  t += 2 * r(8LL * kMaxPartials * (4096 + S));  // per-block partials (upper bound of the grid) and row slots
+  *bytes = t;
+  return LP_OK;
 }
 
 int lp_kernel_times(lp_problem* p, double* ms, int64_t* samples, int32_t n_kernels, int64_t* launches) {

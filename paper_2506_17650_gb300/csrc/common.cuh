@@ -47,6 +47,7 @@ struct Params {
   double floor;
   double b_norm;  // ||b||_2, user units
   double c_norm;  // ||c||_2, user units
+  double refine_tol;  // mixed precision: FP32 -> FP64 hand-over threshold
 };
 
 // Device-resident solver state.  Written only by single-thread control code
@@ -90,6 +91,11 @@ struct DevState {
   double step_d;      // eta * omega
   double sqrt_gp;     // sqrt of gp_norm (0 when it is 0)
   double sqrt_gd;
+  // device-side solve loop (batched kernel)
+  int initial_checked;  // the check before the first attempt has run
+  int phase32;          // mixed precision: still in the FP32 phase
+  int stall;            // checks since the relative KKT error last dropped by 10%
+  double best_kkt;
 };
 
 // Entries of the step-size schedule table (attempt counts below this use the table).
@@ -116,8 +122,11 @@ struct Dev {
   uint8_t* sense;
   Vecs<double> f64;
   Vecs<float> f32;    // null pointers unless mixed precision
-  double* partials;   // [max_grid * kMaxPartials] written by primal/check-primal kernels
-  double* partials2;  // same, written by dual/check-dual kernels
+  // per-block partial sums: [gridAt + binsAt.seg_rows] rows of kMaxPartials,
+  // written by the A^T-row kernels (a block's own sums, then one row per
+  // segmented row); partials2 the same for the A-row kernels
+  double* partials;
+  double* partials2;
   double* work;       // small scratch for setup reductions
   double* work2;      // [max(m, n)] FP64 staging of FP32 vectors read by the host
   const double* step_tab;  // [2 * kStepTab]: 1 - (t+1)^-0.3 and 1 + (t+1)^-0.6 for t < kStepTab
@@ -126,6 +135,16 @@ struct Dev {
   int gridA, gridAt;  // blocks launched for the A / A^T row kernels
   int max_grid;
 };
+
+// Slots of the segmented rows within a partials array, and the rows to sum.
+__host__ __device__ inline double* row_slots_at(const Dev& d, double* part) {
+  return part + (size_t)d.gridAt * kMaxPartials;
+}
+__host__ __device__ inline double* row_slots_a(const Dev& d, double* part) {
+  return part + (size_t)d.gridA * kMaxPartials;
+}
+__host__ __device__ inline int partial_rows_at(const Dev& d) { return d.gridAt + d.binsAt.seg_rows; }
+__host__ __device__ inline int partial_rows_a(const Dev& d) { return d.gridA + d.binsA.seg_rows; }
 
 template <class V>
 __host__ __device__ inline const Vecs<V>& vecs(const Dev& d);

@@ -42,7 +42,12 @@ std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<
   for (int r = 0; r < rows; ++r) width[r] = width_for_length(len[r], widen);
   std::vector<int> perm(rows);
   std::iota(perm.begin(), perm.end(), 0);
-  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return bin_rank(width[a]) < bin_rank(width[b]); });
+  // by bin, then longest first within a bin (a warp's rows get similar lengths;
+  // the heaviest units come first)
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+    const int ra = bin_rank(width[a]), rb = bin_rank(width[b]);
+    return ra != rb ? ra < rb : len[a] > len[b];
+  });
   widths_sorted.resize(rows);
   for (int r = 0; r < rows; ++r) widths_sorted[r] = width[perm[r]];
   return perm;
@@ -198,6 +203,61 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
     }
   }
   return LP_OK;
+}
+
+}  // namespace lpop
+
+namespace lpop {
+
+int segment_length(long long nnz, int grid) {
+  // half the mean work of a block, so that a long row spreads over at least
+  // two blocks' worth of the grid; never below twice the whole-block threshold
+  const long long per_block = grid > 0 ? nnz / grid : nnz;
+  long long len = (per_block / 2 + 1023) / 1024 * 1024;
+  if (len < 2 * kBlockRowThreshold) len = 2 * kBlockRowThreshold;
+  if (len > (1LL << 30)) len = 1LL << 30;
+  return (int)len;
+}
+
+std::vector<int> segment_long_rows(BinTable& bt, const std::vector<int>& rp, int seg_len) {
+  std::vector<int> units;
+  bt.seg_len = 0;
+  bt.seg_rows = 0;
+  if (bt.nbins == 0 || bt.bin[0].width != 0 || seg_len <= 0) return units;
+  // rows of the whole-block bin are sorted longest first: the segmented rows are a prefix
+  const Bin blk = bt.bin[0];
+  int r = blk.row_begin;
+  while (r < blk.row_end && rp[r + 1] - rp[r] > seg_len) {
+    const int segs = (rp[r + 1] - rp[r] + seg_len - 1) / seg_len;
+    for (int t = 0; t < segs; ++t) {
+      units.push_back(r);
+      units.push_back(t);
+    }
+    ++r;
+  }
+  const int rows = r - blk.row_begin;
+  if (rows == 0 || bt.nbins + (r < blk.row_end ? 1 : 0) > kMaxBins) return std::vector<int>();
+  const int nseg_units = (int)units.size() / 2;
+  BinTable out = bt;
+  out.nbins = 0;
+  out.bin[out.nbins++] = Bin{blk.row_begin, r, kSegmented, 0};
+  int unit = nseg_units;
+  if (r < blk.row_end) {
+    out.bin[out.nbins++] = Bin{r, blk.row_end, 0, unit};
+    unit += blk.row_end - r;
+  }
+  for (int b = 1; b < bt.nbins; ++b) {
+    Bin x = bt.bin[b];
+    x.unit_begin = unit;
+    const int per = kBlock / x.width;
+    unit += (x.row_end - x.row_begin + per - 1) / per;
+    out.bin[out.nbins++] = x;
+  }
+  out.nunits = unit;
+  out.seg_len = seg_len;
+  out.seg_rows = rows;
+  bt = out;
+  return units;
 }
 
 }  // namespace lpop

@@ -36,4 +36,13 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
 // Bin table for rows already sorted by bin (widths non-increasing in "work" order).
 BinTable make_bins(const std::vector<int>& widths_sorted);
 
+// Segment length for a matrix of nnz entries processed by `grid` blocks.
+int segment_length(long long nnz, int grid);
+
+// Cut the rows of the whole-block bin longer than seg_len into segments: they
+// become a leading kSegmented bin and the unit numbering of every bin is
+// redone.  Returns the (row, segment index) pair of each segment unit (empty,
+// with bt unchanged, when no row is that long).
+std::vector<int> segment_long_rows(BinTable& bt, const std::vector<int>& rp, int seg_len);
+
 }  // namespace lpop

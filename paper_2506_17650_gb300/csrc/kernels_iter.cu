@@ -22,6 +22,7 @@
 // clamps and sign projections on the integer pipes (ordered keys), step
 // scalars precomputed by the control thread, and block sums done by one warp.
 #include "common.cuh"
+#include "ops.cuh"
 #include "spmv.cuh"
 
 namespace lpop {
@@ -29,151 +30,7 @@ namespace lpop {
 namespace {
 
 template <class V>
-struct StepScalars {
-  int cur;
-  int collect;  // k mod phi == 0: record q / p for the online gradient
-  int pend;     // apply the pending update of this side
-  V eta;
-  V step;  // eta / omega (primal) or eta * omega (dual)
-  V up_scale;
-  V sqrt_gnorm;
-};
-
-template <class V>
-__device__ __forceinline__ StepScalars<V> read_scalars(const DevState* st, bool primal) {
-  StepScalars<V> s;
-  s.cur = st->cur;
-  s.eta = (V)st->eta;
-  s.collect = st->collect;
-  s.step = (V)(primal ? st->step_p : st->step_d);
-  s.pend = primal ? st->pend_p : st->pend_d;
-  s.up_scale = (V)(primal ? st->up_scale_p : st->up_scale_d);
-  s.sqrt_gnorm = (V)(primal ? st->sqrt_gp : st->sqrt_gd);
-  return s;
-}
-
-// One projected online-gradient step of a diagonal preconditioner entry with
-// the chosen learning-rate rule (Section 3.1 OGD, Section 4.1 AdaGrad).
-template <class V>
-__device__ __forceinline__ V ogd_entry(V P, V* G, V grad, const Params& prm, V sqrt_gnorm) {
-  const V alpha = (V)prm.alpha;
-  if (prm.sched == kAdagrad) {
-    const V Gn = *G + grad * grad;
-    *G = Gn;
-    if (Gn > V(0)) P = P - alpha * (grad / sqrt(Gn));
-  } else if (prm.sched == kAdagradNorm) {
-    if (sqrt_gnorm > V(0)) P = P - alpha * (grad / sqrt_gnorm);
-  } else {
-    P = P - alpha * grad;
-  }
-  return fmax(P, (V)prm.floor);
-}
-
-template <class V>
-struct PrimalOp {
-  const V *c, *l, *u, *xc, *xbarc;
-  V *T, *invT, *GT, *q, *xn, *xbarn;
-  Params prm;
-  StepScalars<V> sc;
-  V acc[3];  // sum dx^2 / T, ||g||^2, sum q^2 (per thread; combined across threads in FP64)
-  V pT, piT, pc, px, pl, pu, pxb;  // operands of the row being processed, loaded early
-
-  __device__ __forceinline__ void prefetch(int j) {
-    pT = T[j];
-    piT = invT[j];
-    pc = __ldg(c + j);
-    px = xc[j];
-    pl = __ldg(l + j);
-    pu = __ldg(u + j);
-    if (prm.mode == kPdlp) pxb = xbarc[j];
-  }
-
-  __device__ __forceinline__ void row(int j, const V (&s)[1]) {
-    V Tj = pT, iT = piT;
-    if (sc.pend) {  // pending online update of T_j (rare: once every phi accepted steps)
-      Tj = ogd_entry<V>(Tj, GT + j, sc.up_scale * q[j], prm, sc.sqrt_gnorm);
-      iT = V(1) / Tj;
-      T[j] = Tj;
-      invT[j] = iT;
-    }
-    const V g = pc - s[0];
-    const V x0 = px;
-    const V xh = x0 - sc.step * Tj * g;
-    const V lo = pl, hi = pu;
-    const auto kx = ord_key(xh), kl = ord_key(lo), kh = ord_key(hi);
-    const V x1 = clamp_keys(xh, kx, lo, kl, hi, kh);
-    xn[j] = x1;
-    if (prm.mode == kPdlp) xbarn[j] = pxb + sc.eta * x1;
-    const V dx = x1 - x0;
-    acc[0] += dx * dx * iT;
-    if (sc.collect) {
-      const V gi = (kx >= kl && kx <= kh) ? g : V(0);
-      const V qj = gi * g;
-      q[j] = qj;
-      acc[1] += g * g;
-      acc[2] += qj * qj;
-    }
-  }
-};
-
-template <class V>
-struct DualOp {
-  const V *b, *axc, *yc, *ybarc;
-  const uint8_t* sense;
-  V *S, *invS, *GS, *p, *yn, *axn, *ybarn;
-  Params prm;
-  StepScalars<V> sc;
-  V acc[4];  // sum dy^2 / Sigma, dy . A dx, ||b - A x||^2, sum p^2
-  V pS, piS, pa0, pb, py, pyb;  // operands of the row being processed, loaded early
-  uint8_t psn;
-
-  __device__ __forceinline__ void prefetch(int i) {
-    pS = S[i];
-    piS = invS[i];
-    pa0 = axc[i];
-    pb = __ldg(b + i);
-    py = yc[i];
-    psn = __ldg(sense + i);
-    if (prm.mode == kPdlp) pyb = ybarc[i];
-  }
-
-  __device__ __forceinline__ void row(int i, const V (&s)[1]) {
-    V Si = pS, iS = piS;
-    if (sc.pend) {
-      Si = ogd_entry<V>(Si, GS + i, sc.up_scale * p[i], prm, sc.sqrt_gnorm);
-      iS = V(1) / Si;
-      S[i] = Si;
-      invS[i] = iS;
-    }
-    const V a1 = s[0];
-    const V a0 = pa0;
-    const V bi = pb;
-    const V r = bi - (V(2) * a1 - a0);
-    const V y0 = py;
-    const V yh = y0 + sc.step * Si * r;
-    const uint8_t sn = psn;
-    const auto ky = ord_key(yh);
-    // <= rows keep y <= 0, >= rows keep y >= 0, equality rows are free
-    const bool outside = (sn == kLe && ky > 0) || (sn == kGe && ky < 0);
-    const V y1 = outside ? V(0) : yh;
-    yn[i] = y1;
-    axn[i] = a1;
-    if (prm.mode == kPdlp) ybarn[i] = pyb + sc.eta * y1;
-    const V dy = y1 - y0;
-    acc[0] += dy * dy * iS;
-    acc[1] += dy * (a1 - a0);
-    if (sc.collect) {
-      const V res = bi - a0;
-      const V pi = outside ? V(0) : res * r;
-      p[i] = pi;
-      acc[2] += res * res;
-      acc[3] += pi * pi;
-    }
-  }
-};
-
-template <class V>
-__global__ void __launch_bounds__(kBlock) primal_step_kernel(Dev d, Params prm) {
+__global__ void __launch_bounds__(kBlock, 3) primal_step_kernel(Dev d, Params prm) {
   __shared__ double smem[kBlock * 3];
   const Vecs<V>& v = vecs<V>(d);
   PrimalOp<V> op;
@@ -187,7 +44,7 @@ __global__ void __launch_bounds__(kBlock) primal_step_kernel(Dev d, Params prm) 
   op.acc[0] = op.acc[1] = op.acc[2] = V(0);
   Gather<1, V> g;
   g.x[0] = v.y[cur];
-  for_each_row<1, V, V>(d.binsAt, csr_at<V>(d), g, op, smem);
+  for_each_row<1, V, V>(d.binsAt, csr_at<V>(d), g, op, smem, row_slots_at(d, d.partials));
   double a[3] = {(double)op.acc[0], (double)op.acc[1], (double)op.acc[2]};
   block_sum_smem<3>(a, smem);
   if (threadIdx.x == 0) {
@@ -196,63 +53,8 @@ __global__ void __launch_bounds__(kBlock) primal_step_kernel(Dev d, Params prm) 
   }
 }
 
-// Step control (single thread): adaptive step test of Eq. (6) in the T^-1 /
-// Sigma^-1 weighted norms, next step size, buffer swap, online-update scalars.
-// Works on a register copy of the state and writes it back once.
-__device__ void step_control(const Dev& d, const Params& prm, const double (&t1)[3], const double (&t2)[4]) {
-  DevState s = *d.st;
-  const double eta = s.eta, omega = s.omega;
-  const bool collect = s.collect;
-  s.pend_p = 0;  // applied by this attempt's kernels
-  s.pend_d = 0;
-  s.attempts += 1;
-  bool accept = true;
-  double eta_next = eta;
-  if (prm.mode == kPdlp) {
-    const double movement = omega * t1[0] + t2[0] / omega;
-    const double interaction = fabs(t2[1]);
-    const double eta_max = interaction > 0.0 ? movement / (2.0 * interaction) : INFINITY;
-    accept = eta <= eta_max;
-    const long long t = s.attempts;
-    double f1, f2;
-    if (t < kStepTab) {
-      f1 = __ldg(d.step_tab + t);
-      f2 = __ldg(d.step_tab + kStepTab + t);
-    } else {
-      f1 = 1.0 - pow((double)t + 1.0, -0.3);
-      f2 = 1.0 + pow((double)t + 1.0, -0.6);
-    }
-    eta_next = fmin(f1 * eta_max, f2 * eta);
-    s.last_eta_max = eta_max;
-  }
-  if (accept) {
-    if (collect) {
-      if (!prm.normalize || t1[1] > 0.0) {
-        const double sc = -(eta / omega) * (prm.normalize ? 1.0 / t1[1] : 1.0);
-        s.up_scale_p = sc;
-        s.pend_p = 1;
-        if (prm.sched == kAdagradNorm) s.gp_norm += sc * sc * t1[2];
-      }
-      if (!prm.normalize || t2[2] > 0.0) {
-        const double sc = -(eta * omega) * (prm.normalize ? 1.0 / t2[2] : 1.0);
-        s.up_scale_d = sc;
-        s.pend_d = 1;
-        if (prm.sched == kAdagradNorm) s.gd_norm += sc * sc * t2[3];
-      }
-    }
-    if (prm.mode == kPdlp) s.wsum += eta;
-    s.cur ^= 1;
-    s.k += 1;
-  }
-  s.eta = eta_next;
-  s.last_accept = accept ? 1 : 0;
-  s.counter = 0;
-  refresh_derived(s, prm.phi);
-  *d.st = s;
-}
-
 template <class V>
-__global__ void __launch_bounds__(kBlock) dual_step_kernel(Dev d, Params prm) {
+__global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm) {
   __shared__ double smem[kBlock * 4];
   const Vecs<V>& v = vecs<V>(d);
   DualOp<V> op;
@@ -266,7 +68,7 @@ __global__ void __launch_bounds__(kBlock) dual_step_kernel(Dev d, Params prm) {
   op.acc[0] = op.acc[1] = op.acc[2] = op.acc[3] = V(0);
   Gather<1, V> g;
   g.x[0] = v.x[nxt];  // x+ written by the primal kernel
-  for_each_row<1, V, V>(d.binsA, csr_a<V>(d), g, op, smem);
+  for_each_row<1, V, V>(d.binsA, csr_a<V>(d), g, op, smem, row_slots_a(d, d.partials2));
   double a[4] = {(double)op.acc[0], (double)op.acc[1], (double)op.acc[2], (double)op.acc[3]};
   block_sum_smem<4>(a, smem);
   __shared__ int s_last;
@@ -281,9 +83,13 @@ __global__ void __launch_bounds__(kBlock) dual_step_kernel(Dev d, Params prm) {
   if (!s_last) return;
   __threadfence();
   double t1[3], t2[4];
-  sum_partials<3>(d.partials, d.gridAt, t1, smem);
-  sum_partials<4>(d.partials2, d.gridA, t2, smem);
-  if (threadIdx.x == 0) step_control(d, prm, t1, t2);
+  sum_partials<3>(d.partials, partial_rows_at(d), t1, smem);
+  sum_partials<4>(d.partials2, partial_rows_a(d), t2, smem);
+  if (threadIdx.x == 0) {
+    DevState s = *d.st;  // register copy, written back once
+    step_control_state(s, prm, d.step_tab, t1, t2);
+    *d.st = s;
+  }
 }
 
 // Apply a pending update of T and Sigma immediately (used before debug reads).

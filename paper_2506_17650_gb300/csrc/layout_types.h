@@ -16,9 +16,13 @@ enum Mode : int { kPlain = 0, kPdlp = 1 };
 enum Sched : int { kAdagrad = 0, kAdagradNorm = 1, kConst = 2 };
 
 // One row-length class: rows [row_begin, row_end) of a permuted CSR matrix,
-// handled with `width` lanes per row (1..32), or a whole block per row when
-// width == 0.  Work units: one row per unit for width 0, kBlock/width rows
-// per unit otherwise; units of all bins are numbered consecutively.
+// handled with `width` lanes per row (1..32), a whole block per row when
+// width == 0, or, when width == kSegmented, cut into segments of seg_len
+// entries that different blocks reduce concurrently.  Work units: one row per
+// unit for width 0, kBlock/width rows per unit for 1..32, one segment per unit
+// for kSegmented; units of all bins are numbered consecutively.
+constexpr int kSegmented = -1;
+
 struct Bin {
   int row_begin;
   int row_end;
@@ -30,6 +34,12 @@ struct BinTable {
   int nbins;
   int nunits;
   Bin bin[kMaxBins];
+  // segmented bin (at most one, always bin 0 when present)
+  int seg_len;             // entries per segment (0: no segmented bin)
+  int seg_rows;            // rows in the segmented bin
+  const int* seg_unit;     // device [2 * segment units]: (row, segment index); a row's segments are consecutive
+  double* seg_sum;         // device [2 * segment units]: block sums of the segments (up to two vectors)
+  unsigned int* ticket;    // device [seg_rows]: segments of the row finished in the running launch
 };
 
 }  // namespace lpop

@@ -5,11 +5,14 @@
 //     s[q] = sum_k M.v[k] * x_q[M.ci[k]],   k in [M.rp[r], M.rp[r+1])
 // in the accumulator type Acc (matrix and vectors of type V) and hands them to
 // op.row(r, s); op.prefetch(r) is called first, before the row's loads, so an
-// op can start loading its own per-row operands early.  Rows up to 16 entries use one lane, longer rows 4..32 lanes
-// that stride through the row so that one warp's loads of M.v and M.ci are
-// contiguous, very long rows a whole block.  Lane sums are combined by a fixed
+// op can start loading its own per-row operands early.  Rows up to 16 entries
+// use one lane, longer rows 4..32 lanes that stride through the row so that
+// one warp's loads of M.v and M.ci are contiguous, long rows a whole block,
+// and the longest rows several blocks (segments).  Lane sums are combined by a fixed
 // shuffle tree, so results do not depend on scheduling.
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -19,6 +22,42 @@ template <int NV, class V>
 struct Gather {
   const V* x[NV];
 };
+
+// Entries handled per lane per round: all their index/value loads are issued,
+// then all gathers, then the FMAs, so each lane keeps kChunk independent
+// loads in flight instead of one dependent load chain per entry.
+constexpr int kChunk = 8;
+
+// s[q] += sum over this lane's entries k = k0 + u * stride (u < kChunk, k < end), in order of k.
+template <int NV, class V, class Acc>
+__device__ __forceinline__ void chunk_dot(int k0, int end, int stride, const CsrT<V>& M, const Gather<NV, V>& g,
+                                          Acc (&s)[NV]) {
+  int c[kChunk];
+  Acc a[kChunk];
+#pragma unroll
+  for (int u = 0; u < kChunk; ++u) {
+    const int k = k0 + u * stride;
+    const bool ok = k < end;
+    c[u] = ok ? __ldg(M.ci + k) : -1;
+    a[u] = ok ? (Acc)__ldg(M.v + k) : Acc(0);
+  }
+  // entries of this lane in the chunk, and their maximum over the warp's active
+  // lanes: FMAs past it are skipped by a warp-uniform branch (on GB300 a
+  // predicated-off FP64 instruction still costs its issue slots)
+  const int mine = end > k0 ? min(kChunk, (end - k0 + stride - 1) / stride) : 0;
+  const int most = __reduce_max_sync(__activemask(), mine);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    Acc xv[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) xv[u] = c[u] >= 0 ? (Acc)__ldg(g.x[q] + c[u]) : Acc(0);
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      if (u >= most) break;
+      if (u < mine) s[q] = fma(a[u], xv[u], s[q]);
+    }
+  }
+}
 
 template <int W, int NV, class V, class Acc, class Op>
 __device__ __forceinline__ void vec_rows(int first, int row_end, const CsrT<V>& M, const Gather<NV, V>& g,
@@ -32,13 +71,7 @@ __device__ __forceinline__ void vec_rows(int first, int row_end, const CsrT<V>& 
     if (lane == 0) op.prefetch(row);  // epilogue operands load while the row is gathered
     const int beg = __ldg(M.rp + row);
     const int end = __ldg(M.rp + row + 1);
-#pragma unroll 4
-    for (int k = beg + lane; k < end; k += W) {
-      const Acc a = (Acc)__ldg(M.v + k);
-      const int c = __ldg(M.ci + k);
-#pragma unroll
-      for (int q = 0; q < NV; ++q) s[q] = fma(a, (Acc)__ldg(g.x[q] + c), s[q]);
-    }
+    for (int k0 = beg + lane; k0 < end; k0 += kChunk * W) chunk_dot<NV, V, Acc>(k0, end, W, M, g, s);
   }
   if (W > 1) {
 #pragma unroll
@@ -50,22 +83,30 @@ __device__ __forceinline__ void vec_rows(int first, int row_end, const CsrT<V>& 
   if (lane == 0 && row < row_end) op.row(row, s);
 }
 
+// Block-wide FP64 sums of the entries [beg, end) of one row (valid in warp 0).
+template <int NV, class V, class Acc>
+__device__ __forceinline__ void block_dot(int beg, int end, const CsrT<V>& M, const Gather<NV, V>& g, double (&s)[NV],
+                                          double* smem) {
+#pragma unroll
+  for (int q = 0; q < NV; ++q) s[q] = 0.0;
+  const int stride = (int)blockDim.x;
+  for (int k0 = beg + (int)threadIdx.x; k0 < end; k0 += kChunk * stride) {
+    Acc t[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) t[q] = Acc(0);
+    chunk_dot<NV, V, Acc>(k0, end, stride, M, g, t);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) s[q] += (double)t[q];
+  }
+  block_sum<NV>(s, smem);
+}
+
 template <int NV, class V, class Acc, class Op>
 __device__ __forceinline__ void block_row(int row, const CsrT<V>& M, const Gather<NV, V>& g, Op& op,
                                           double* smem) {
   if (threadIdx.x == 0) op.prefetch(row);
-  const int beg = __ldg(M.rp + row);
-  const int end = __ldg(M.rp + row + 1);
   double s[NV];  // the block-wide sum of a long row is formed in FP64
-#pragma unroll
-  for (int q = 0; q < NV; ++q) s[q] = 0.0;
-  for (int k = beg + (int)threadIdx.x; k < end; k += (int)blockDim.x) {
-    const double a = (double)__ldg(M.v + k);
-    const int c = __ldg(M.ci + k);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) s[q] = fma(a, (double)__ldg(g.x[q] + c), s[q]);
-  }
-  block_sum<NV>(s, smem);
+  block_dot<NV, V, Acc>(__ldg(M.rp + row), __ldg(M.rp + row + 1), M, g, s, smem);
   if (threadIdx.x == 0) {
     Acc r[NV];
 #pragma unroll
@@ -74,17 +115,102 @@ __device__ __forceinline__ void block_row(int row, const CsrT<V>& M, const Gathe
   }
 }
 
-// smem must hold 32 * NV doubles.
+// Run op.row with the op's reduction accumulators diverted into slot[0..): the
+// contribution of a segmented row is kept apart from the block's own partial
+// sums, so the totals do not depend on which block finishes the row.
+template <class Acc, class Op, int NV>
+__device__ __forceinline__ void row_into_slot(Op& op, int row, const Acc (&r)[NV], double* slot) {
+  constexpr int NA = (int)(sizeof(op.acc) / sizeof(op.acc[0]));
+  using A = typename std::remove_reference<decltype(op.acc[0])>::type;
+  A saved[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    saved[q] = op.acc[q];
+    op.acc[q] = A(0);
+  }
+  op.row(row, r);
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    slot[q] = (double)op.acc[q];
+    op.acc[q] = saved[q];
+  }
+}
+
+// Ops that keep per-block reduction accumulators (member `acc`).
+template <class Op, class = void>
+struct HasAcc : std::false_type {};
+template <class Op>
+struct HasAcc<Op, std::void_t<decltype(std::declval<Op&>().acc)>> : std::true_type {};
+
+// One segment of a segmented row, published for the row's other segments;
+// the block that completes the row's last segment adds the segment sums in
+// segment order and runs the epilogue into the row's slot.
 template <int NV, class V, class Acc, class Op>
-__device__ __forceinline__ void for_each_row(const BinTable& bt, const CsrT<V>& M, const Gather<NV, V>& g, Op& op,
-                                             double* smem) {
-  for (int u = blockIdx.x; u < bt.nunits; u += gridDim.x) {
+__device__ __forceinline__ void segment_reduce(const BinTable& bt, int local, int row, int seg, const CsrT<V>& M,
+                                               const Gather<NV, V>& g, Op& op, double* smem, double* row_slots) {
+  static_assert(NV <= 2, "segment sums hold up to two vectors");
+  const int r0 = __ldg(M.rp + row), r1 = __ldg(M.rp + row + 1);
+  const int beg = r0 + seg * bt.seg_len;
+  const int end = min(beg + bt.seg_len, r1);
+  double s[NV];
+  block_dot<NV, V, Acc>(beg, end, M, g, s, smem);
+  if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) bt.seg_sum[2 * local + q] = s[q];
+  __threadfence();
+  const int id = row - bt.bin[0].row_begin;
+  const unsigned int nseg = (unsigned int)((r1 - r0 + bt.seg_len - 1) / bt.seg_len);
+  if (atomicAdd(bt.ticket + id, 1u) != nseg - 1) return;
+  __threadfence();
+  const int first = local - seg;
+  double tot[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = 0.0;
+  for (int t = 0; t < (int)nseg; ++t) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] += __ldcg(bt.seg_sum + 2 * (first + t) + q);
+  }
+  bt.ticket[id] = 0u;  // ready for the next launch
+  Acc r[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) r[q] = (Acc)tot[q];
+  op.prefetch(row);
+  row_into_slot<Acc>(op, row, r, row_slots + (size_t)id * kMaxPartials);
+}
+
+// A unit of the segmented bin.  With row_slots (one row of kMaxPartials
+// doubles per segmented row, for ops with reduction accumulators) segments
+// are reduced by separate blocks (segment_reduce).  Without, the unit of
+// segment 0 reduces the whole row and the others do nothing.
+template <int NV, class V, class Acc, class Op>
+__device__ __forceinline__ void segment_unit(const BinTable& bt, int local, const CsrT<V>& M, const Gather<NV, V>& g,
+                                             Op& op, double* smem, double* row_slots) {
+  const int row = __ldg(bt.seg_unit + 2 * local);
+  const int seg = __ldg(bt.seg_unit + 2 * local + 1);
+  if constexpr (HasAcc<Op>::value) {
+    if (row_slots) {
+      segment_reduce<NV, V, Acc>(bt, local, row, seg, M, g, op, smem, row_slots);
+      return;
+    }
+  }
+  if (seg == 0) block_row<NV, V, Acc>(row, M, g, op, smem);
+}
+
+// Work units first_unit, first_unit + unit_stride, ... of the table (one block
+// per unit at a time).  smem must hold 32 * NV doubles.  row_slots: see
+// segment_unit.
+template <int NV, class V, class Acc, class Op>
+__device__ __forceinline__ void for_each_row_range(const BinTable& bt, const CsrT<V>& M, const Gather<NV, V>& g,
+                                                   Op& op, double* smem, int first_unit, int unit_stride,
+                                                   double* row_slots = nullptr) {
+  for (int u = first_unit; u < bt.nunits; u += unit_stride) {
     int b = 0;
     while (b + 1 < bt.nbins && u >= bt.bin[b + 1].unit_begin) ++b;
     const int row_begin = bt.bin[b].row_begin;
     const int row_end = bt.bin[b].row_end;
     const int local = u - bt.bin[b].unit_begin;
     switch (bt.bin[b].width) {
+      case kSegmented: segment_unit<NV, V, Acc>(bt, local, M, g, op, smem, row_slots); break;
       case 0: block_row<NV, V, Acc>(row_begin + local, M, g, op, smem); break;
       case 1: vec_rows<1, NV, V, Acc>(row_begin + local * kBlock, row_end, M, g, op); break;
       case 2: vec_rows<2, NV, V, Acc>(row_begin + local * (kBlock / 2), row_end, M, g, op); break;
@@ -96,7 +222,12 @@ __device__ __forceinline__ void for_each_row(const BinTable& bt, const CsrT<V>& 
   }
 }
 
-// Rows per work unit for a bin width (0 = block per row).
-__host__ __device__ inline int rows_per_unit(int width) { return width == 0 ? 1 : kBlock / width; }
+// All work units, spread over the grid's blocks in a grid-stride loop (the
+// longest rows are numbered first, so they start first).
+template <int NV, class V, class Acc, class Op>
+__device__ __forceinline__ void for_each_row(const BinTable& bt, const CsrT<V>& M, const Gather<NV, V>& g, Op& op,
+                                             double* smem, double* row_slots = nullptr) {
+  for_each_row_range<NV, V, Acc>(bt, M, g, op, smem, blockIdx.x, gridDim.x, row_slots);
+}
 
 }  // namespace lpop

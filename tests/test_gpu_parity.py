@@ -104,6 +104,8 @@ CASES = {
     "rowmix_pdlp": (lambda: lpgen.row_length_mix(0), oracle.Options(alpha=1e-3, phi=20)),
     "transport_small_pdlp": (lambda: lpgen.transport(0, 1500, 1500, 12000), oracle.Options(alpha=1e-4, phi=20)),
     "alpha0_pdlp": (lambda: lpgen.mixed_small(3), oracle.Options(alpha=0.0, phi=1)),
+    # rows of A and of A^T longer than a segment (4096 entries here): reduced by several blocks
+    "long_rows_pdlp": (lambda: lpgen.long_rows(0), oracle.Options(alpha=1e-3, phi=1)),
 }
 
 
