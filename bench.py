@@ -210,6 +210,16 @@ def kernel_bytes(m, n, nnz):
     return primal, dual
 
 
+# DRAM bytes (read + write) per launch of a dominant kernel from one ncu
+# capture, with the algorithmic bytes of the captured launch: a capture of a
+# smaller instance of the same workload is scaled by the algorithmic bytes
+# (the units processed).  Re-take a capture whenever the kernel changes.
+NCU_TRAFFIC = {
+    ("transport", "dual"): (9_224_704, 9_850_000, "profiles/transport_dual_step_full.md"),
+    ("powerlaw", "primal"): (68_640_512, 70_898_060, "profiles/powerlaw_primal_step_full.md (scale 0.1)"),
+}
+
+
 def kernel_fp64_ops(m, n, nnz):
     """FP64 operations per launch the method needs (an FMA counts once): one
     FMA per nonzero of the product, and per row the step's arithmetic --
@@ -381,7 +391,9 @@ def gpu_arm(args):
                 "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth)",
                 "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": None,
+                "traffic": (NCU_TRAFFIC[(kind, dom)][0] * dom_bytes / NCU_TRAFFIC[(kind, dom)][1]
+                            if (kind, dom) in NCU_TRAFFIC else None),
+                "traffic_source": NCU_TRAFFIC[(kind, dom)][2] if (kind, dom) in NCU_TRAFFIC else None,
                 "algorithmic_bytes_per_launch": dom_bytes,
                 "avg_launch_us": 1e3 * dom_ms,
                 "other_kernel_avg_us": 1e3 * (avg_dual_ms if dom == "primal" else avg_primal_ms),

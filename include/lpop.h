@@ -200,7 +200,8 @@ int lp_get_scaling(lp_problem* p, double* dr, double* dc, double* scal);
  *          recorded (0/1), initial check done (0/1), 0
  * lp_set_state takes the same layout (all three arrays required) and makes it
  * the state the next lp_solve continues from; the iteration limit of lp_solve
- * stays cumulative in `attempts`.  Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
+ * stays cumulative in `attempts`.  Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA,
+ * LP_ERR_INVALID_INPUT (lp_set_state: eta or omega not finite and positive).
  */
 int lp_get_state(lp_problem* p, double* vec_n, double* vec_m, double* scal);
 int lp_set_state(lp_problem* p, const double* vec_n, const double* vec_m, const double* scal);

@@ -169,11 +169,12 @@ int init_state(lp_problem* p) {
   s0.cur = 0;
   s0.eta = p->eta0;
   s0.omega = p->omega0;
+  s0.inv_omega = 1.0 / p->omega0;
   s0.tol = 1e-4;
   s0.k_prev = INFINITY;
   s0.phase32 = p->mixed ? 1 : 0;
   s0.best_kkt = INFINITY;
-  refresh_derived(s0, p->prm.phi);
+  refresh_derived(s0, p->prm.phi, p->prm.sched);
   CK(cudaMemcpyAsync(p->d.st, &s0, sizeof(s0), cudaMemcpyHostToDevice, p->stream));
   launch_init_vectors(p->d, p->stream);
   launch_spmv_binned(p->d.A, p->d.binsA, p->d.gridA, p->d.f64.x[0], p->d.f64.ax[0], p->stream);
@@ -515,6 +516,8 @@ int get_state_impl(lp_problem* p, double* vn, double* vm, double* scal) {
 }
 
 int set_state_impl(lp_problem* p, const double* vn, const double* vm, const double* scal) {
+  if (!(std::isfinite(scal[0]) && scal[0] > 0.0 && std::isfinite(scal[1]) && scal[1] > 0.0))
+    return set_err(p, LP_ERR_INVALID_INPUT, "state: eta and omega must be finite and positive");
   TRY(select_device(p));
   CK(cudaStreamSynchronize(p->stream));
   DevState hs;
@@ -528,6 +531,7 @@ int set_state_impl(lp_problem* p, const double* vn, const double* vm, const doub
   for (int k = 0; k < 6; ++k) TRY(upload_vec(p, dm[k], vm + (size_t)k * m, m, p->prow));
   hs.eta = scal[0];
   hs.omega = scal[1];
+  hs.inv_omega = 1.0 / hs.omega;
   hs.wsum = scal[2];
   hs.gp_norm = scal[3];
   hs.gd_norm = scal[4];
@@ -547,7 +551,7 @@ int set_state_impl(lp_problem* p, const double* vn, const double* vm, const doub
   hs.adopt_avg = 0;
   hs.initial_checked = scal[14] != 0.0;
   hs.phase32 = p->fp32_phase ? 1 : 0;
-  refresh_derived(hs, p->prm.phi);
+  refresh_derived(hs, p->prm.phi, p->prm.sched);
   CK(cudaMemcpyAsync(p->d.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, p->stream));
   launch_inverse_preconditioners(p->d, false, p->stream);
   if (p->fp32_phase) launch_demote_state(p->d, p->stream);  // the FP32 phase continues from the imported state
@@ -983,7 +987,7 @@ int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, in
   // segmented rows (segments are at least 4096 entries): at most S rows and 2 S units per matrix
   const long long S = nnz / 4096 + 1;
   t += 2 * (r(8LL * 2 * S) + r(16LL * 2 * S) + r(4LL * S));
-  t += 2 * r(8LL * kMaxPartials * (4096 + S));  // per-block partials (upper bound of the grid) and row slots
+  t += 2 * r(8LL * kMaxPartials * (4096 + S));  // per-block records (upper bound of the grid) and row slots
   *bytes = t;
   return LP_OK;
 }

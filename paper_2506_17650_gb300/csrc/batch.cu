@@ -150,7 +150,7 @@ __device__ void team_check(const Dev& d, const Params& prm, DevState& s, int ran
   team_reduce<8>(p2, blk, slots + 17, T, wide);
   if (threadIdx.x == 0) {
     check_control(&s, prm, p1, p2, eval_only, avg ? 1 : 0);
-    refresh_derived(s, prm.phi);
+    refresh_derived(s, prm.phi, prm.sched);
   }
   __syncthreads();
   apply_decision<V>(d, s, rank * blockDim.x + threadIdx.x, T * blockDim.x);
@@ -253,7 +253,11 @@ __device__ bool team_round(const Member& mb, DevState& s, int& budget, int rank,
       t2[0] = op.acc[0]; t2[1] = op.acc[1]; t2[2] = op.acc[2]; t2[3] = op.acc[3];
     }
     team_reduce<4>(t2, blk, slots + 3, T, wide);
-    if (threadIdx.x == 0) step_control_state(s, prm, d.step_tab, t1, t2);
+    if (threadIdx.x == 0) {
+      double f1, f2;
+      step_factors(d.step_tab, s.attempts + 1, &f1, &f2);
+      step_control_state(s, prm, f1, f2, t1, t2);
+    }
     __syncthreads();
     --budget;
     if (s.attempts % prm.check_every == 0) {

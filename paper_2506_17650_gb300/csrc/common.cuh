@@ -59,6 +59,7 @@ struct DevState {
   long long attempts;
   double eta;
   double omega;
+  double inv_omega;  // 1 / omega, set wherever omega is
   double wsum;    // sum of eta over accepted steps since the last restart
   double tol;
   // pending online update, applied by the next primal / dual kernel
@@ -101,13 +102,29 @@ struct DevState {
 // Entries of the step-size schedule table (attempt counts below this use the table).
 constexpr int kStepTab = 1 << 20;
 
-// Refresh the derived scalars of a state (host and device).
-__host__ __device__ inline void refresh_derived(DevState& s, int phi) {
+// Refresh the derived scalars of a state (host and device).  Runs once per
+// attempt in a single thread, where every FP64 division and square root is
+// a long dependent chain on GB300: 1/omega is kept with omega, and the
+// square roots are taken only for the scheduler that uses them.
+__host__ __device__ inline void refresh_derived(DevState& s, int phi, int sched) {
   s.collect = phi > 0 && (s.k % phi) == 0;
-  s.step_p = s.eta / s.omega;
+  s.step_p = s.eta * s.inv_omega;
   s.step_d = s.eta * s.omega;
-  s.sqrt_gp = s.gp_norm > 0.0 ? sqrt(s.gp_norm) : 0.0;
-  s.sqrt_gd = s.gd_norm > 0.0 ? sqrt(s.gd_norm) : 0.0;
+  const bool norm = sched == kAdagradNorm;
+  s.sqrt_gp = norm && s.gp_norm > 0.0 ? sqrt(s.gp_norm) : 0.0;
+  s.sqrt_gd = norm && s.gd_norm > 0.0 ? sqrt(s.gd_norm) : 0.0;
+}
+
+// Factors of the next-step-size rule for attempt t: 1 - (t+1)^-0.3 and
+// 1 + (t+1)^-0.6 (tabulated below kStepTab).
+__device__ inline void step_factors(const double* step_tab, long long t, double* f1, double* f2) {
+  if (t < kStepTab) {
+    *f1 = __ldg(step_tab + t);
+    *f2 = __ldg(step_tab + kStepTab + t);
+  } else {
+    *f1 = 1.0 - pow((double)t + 1.0, -0.3);
+    *f2 = 1.0 + pow((double)t + 1.0, -0.6);
+  }
 }
 
 // All device buffers of one problem.
@@ -122,9 +139,9 @@ struct Dev {
   uint8_t* sense;
   Vecs<double> f64;
   Vecs<float> f32;    // null pointers unless mixed precision
-  // per-block partial sums: [gridAt + binsAt.seg_rows] rows of kMaxPartials,
-  // written by the A^T-row kernels (a block's own sums, then one row per
-  // segmented row); partials2 the same for the A-row kernels
+  // partial sums of the A^T-row kernels, records of kMaxPartials doubles:
+  // [gridAt] one per block, then [binsAt.seg_rows] one per segmented row;
+  // partials2 the same for the A-row kernels
   double* partials;
   double* partials2;
   double* work;       // small scratch for setup reductions
@@ -136,7 +153,7 @@ struct Dev {
   int max_grid;
 };
 
-// Slots of the segmented rows within a partials array, and the rows to sum.
+// Slots of the segmented rows within a partials array; records of a partials array.
 __host__ __device__ inline double* row_slots_at(const Dev& d, double* part) {
   return part + (size_t)d.gridAt * kMaxPartials;
 }
@@ -234,47 +251,106 @@ __device__ __forceinline__ V clamp_keys(V v, K kv, V lo, K kl, V hi, K kh) {
   return kv > kh ? hi : r;
 }
 
-// Sum `rows` partial records of width N (stride kMaxPartials) in a fixed order;
-// result in thread 0.  Runs in one block on the critical path of every step,
-// so each thread first issues all of its loads (up to 4 records, independent)
-// and only then adds: one L2 round trip instead of one per record.
+// Reductions across blocks.  Every block of a row kernel stores one record
+// of its partial sums.  The records of an A^T-row kernel are folded into the
+// records of the A-row kernel that follows it: block b of that kernel copies
+// records b, b + grid, ... (at most kFold) into shared memory while it works
+// (cp.async, no registers held) and adds them, in that order, to its own
+// record.  The last block of the A-row kernel then sums all records with the
+// whole block.  Every sum has a fixed order, so results do not depend on
+// which block finishes when.
+constexpr int kFold = 8;
+
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  const unsigned int sa = (unsigned int)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Start copying this block's share of `count` records (N fields each) into
+// fold[kFold * N]; returns how many records it is.  Before reading fold:
+// cp_async_wait_all() in every thread, then a barrier.
 template <int N>
-__device__ inline void sum_partials(const double* part, int rows, double (&out)[N], double* smem) {
-#pragma unroll
-  for (int q = 0; q < N; ++q) out[q] = 0.0;
-  for (int r0 = threadIdx.x; r0 < rows; r0 += 4 * blockDim.x) {
-    double v[4][N];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = r0 + u * blockDim.x;
-#pragma unroll
-      for (int q = 0; q < N; ++q) v[u][q] = r < rows ? __ldcg(part + (size_t)r * kMaxPartials + q) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-#pragma unroll
-      for (int q = 0; q < N; ++q) out[q] += v[u][q];
-    }
+__device__ inline int fold_begin(const double* rec, int count, double* fold) {
+  const int b = (int)blockIdx.x, g = (int)gridDim.x;
+  const int k = b < count ? min(kFold, (count - 1 - b) / g + 1) : 0;
+  for (int t = (int)threadIdx.x; t < k * N; t += (int)blockDim.x) {
+    const int r = t / N, q = t - r * N;
+    cp_async8(fold + t, rec + (size_t)(b + r * g) * kMaxPartials + q);
   }
-  block_sum<N>(out, smem);
+  return k;
 }
 
-// Write this block's partial sums; returns true (in every thread) for the last block to finish.
+// Records not folded by a grid of `grid` blocks: [kFold * grid, count).
+__host__ __device__ inline int unfolded_first(int grid) { return kFold * grid; }
+
+// Store this block's record (thread 0 holds v); returns true, in every
+// thread, in the last block to finish.
 template <int N>
-__device__ inline bool publish_partials(double (&v)[N], double* part, unsigned int* counter, double* smem) {
-  block_sum<N>(v, smem);
-  __shared__ int s_last;
+__device__ inline bool publish_last(const double (&v)[N], double* part, unsigned int* counter, int* s_flag) {
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < N; ++q) part[(size_t)blockIdx.x * kMaxPartials + q] = v[q];
     __threadfence();
-    unsigned int t = atomicAdd(counter, 1u);
-    s_last = (t == gridDim.x - 1);
+    *s_flag = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  const bool last = s_last != 0;
-  if (last) __threadfence();
-  return last;
+  if (*s_flag) __threadfence();
+  return *s_flag != 0;
+}
+
+// Field-wise totals of records [0, count) of rec (fields 0..N-1) plus records
+// [0, count2) of rec2 (their fields 0..N2-1 added to fields q2..q2+N2-1),
+// with the whole block and in a fixed order; the totals end up in thread 0.
+// GB300 runs FP64 at 2 lanes per SM per cycle, so one block's reduction is
+// laid out for full lanes: thread t adds field t % N of every (256 / N)-th
+// record, then warp 0 adds the slices (32 / N lanes per field) and the lanes.
+// smem must hold blockDim.x + 32 doubles.
+template <int N, int N2>
+__device__ inline void block_sum_records(const double* rec, int count, const double* rec2, int count2, int q2,
+                                         double (&out)[N], double* smem) {
+  static_assert(N <= 32 && N2 <= N, "record layout");
+  const int t = (int)threadIdx.x;
+  const int S = (int)blockDim.x / N;  // slices
+  const int q = t % N, sl = t / N;
+  double acc = 0.0;
+  if (sl < S) {
+    for (int r0 = sl; r0 < count; r0 += 4 * S) {  // up to 4 independent loads, then the adds
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + u * S;
+        v[u] = r < count ? __ldcg(rec + (size_t)r * kMaxPartials + q) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc += v[u];
+    }
+    if (q >= q2 && q < q2 + N2) {
+      for (int r = sl; r < count2; r += S) acc += __ldcg(rec2 + (size_t)r * kMaxPartials + (q - q2));
+    }
+  }
+  smem[t] = acc;
+  __syncthreads();
+  if (t < 32) {
+    constexpr int P = 32 / N;  // lanes per field
+    double part = 0.0;
+    if (t < N * P) {
+      const int fq = t % N, fp = t / N;
+      for (int x = fp; x < S; x += P) part += smem[x * N + fq];
+    }
+    smem[blockDim.x + t] = part;
+    __syncwarp();
+    if (t < N) {
+      double tot = 0.0;
+      for (int x = 0; x < P; ++x) tot += smem[blockDim.x + x * N + t];
+      smem[t] = tot;  // slice values are no longer needed
+    }
+    __syncwarp();
+    if (t == 0) {
+#pragma unroll
+      for (int f = 0; f < N; ++f) out[f] = smem[f];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

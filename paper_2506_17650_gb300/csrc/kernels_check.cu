@@ -23,7 +23,7 @@ namespace {
 
 template <bool AVG, class V>
 __global__ void __launch_bounds__(kBlock) check_primal_kernel(Dev d) {
-  __shared__ double smem[32 * kMaxPartials];
+  __shared__ double smem[kBlock * 10];
   constexpr int NV = AVG ? 2 : 1;
   const Vecs<V>& v = vecs<V>(d);
   const DevState* st = d.st;
@@ -39,17 +39,19 @@ __global__ void __launch_bounds__(kBlock) check_primal_kernel(Dev d) {
   g.x[0] = v.y[cur];
   if (NV > 1) g.x[NV - 1] = v.ybar[cur];
   for_each_row<NV, V, double>(d.binsAt, csr_at<V>(d), g, op, smem, row_slots_at(d, d.partials));
-  block_sum<10>(op.acc, smem);
+  block_sum_smem<10>(op.acc, smem);
   if (threadIdx.x == 0) {
-    double* part = d.partials + (size_t)blockIdx.x * kMaxPartials;
+    double* rec = d.partials + (size_t)blockIdx.x * kMaxPartials;
 #pragma unroll
-    for (int q = 0; q < 10; ++q) part[q] = op.acc[q];
+    for (int q = 0; q < 10; ++q) rec[q] = op.acc[q];
   }
 }
 
 template <bool AVG, class V>
 __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, int eval_only) {
-  __shared__ double smem[32 * kMaxPartials];
+  __shared__ double smem[kBlock * 8];
+  __shared__ double fold[kFold * 10];
+  const int nfold = fold_begin<10>(d.partials, partial_rows_at(d), fold);
   const Vecs<V>& v = vecs<V>(d);
   DevState* st = d.st;
   const int cur = st->cur;
@@ -73,16 +75,36 @@ __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, i
     const int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) op.row(i, s0);
   }
-  const bool last = publish_partials<8>(op.acc, d.partials2, &st->counter, smem);
-  if (!last) return;
-  double p1[10], p2[8];
-  sum_partials<10>(d.partials, partial_rows_at(d), p1, smem);
+  block_sum_smem<8>(op.acc, smem);
+  cp_async_wait_all();
+  __syncthreads();
+  double rec[18];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) rec[q] = op.acc[q];
+#pragma unroll
+  for (int q = 8; q < 18; ++q) rec[q] = 0.0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < nfold; ++k) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) rec[8 + q] += fold[10 * k + q];
+    }
+  }
+  __shared__ int s_last;
+  if (!publish_last<18>(rec, d.partials2, &st->counter, &s_last)) return;
+  double tot[18];
   // the segmented rows of A write their slots only when the average's product runs
-  sum_partials<8>(d.partials2, AVG ? partial_rows_a(d) : d.gridA, p2, smem);
+  const int f0 = unfolded_first(d.gridA), np = partial_rows_at(d);
+  block_sum_records<18, 10>(d.partials2, AVG ? partial_rows_a(d) : d.gridA, d.partials + (size_t)f0 * kMaxPartials,
+                            np > f0 ? np - f0 : 0, 8, tot, smem);
+  double p1[10], p2[8];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) p1[q] = tot[8 + q];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) p2[q] = tot[q];
   if (threadIdx.x == 0) {
     DevState s = *st;  // register copy, written back once
     check_control(&s, prm, p1, p2, eval_only, avg_ok);
-    refresh_derived(s, prm.phi);  // omega may have changed at a restart
+    refresh_derived(s, prm.phi, prm.sched);  // omega may have changed at a restart
     s.counter = 0;
     *st = s;
   }

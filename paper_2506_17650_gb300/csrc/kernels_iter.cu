@@ -8,8 +8,9 @@
 //   dual_step:   rows i of A.  (A x+)_i, r_i = b_i - (2 A x+ - A x)_i,
 //                y+_i = proj_sense(y_i + eta omega Sigma_i r_i)              (Eq. (6), line 2)
 //                plus partial sums and p_i = (b - A x)_i r_i I(y_half_i in cone).
-//                Its last block to finish sums all partials in a fixed order
-//                and runs the step control: accept/reject (adaptive step),
+//                Its blocks fold the primal kernel's per-block sums into their
+//                own, and its last block to finish sums all of them in a
+//                fixed order and runs the step control: accept/reject (adaptive step),
 //                next eta, swap of the double buffers, and the scalars of a
 //                pending online update of T and Sigma (Eq. (7), Algorithm 1).
 //
@@ -48,14 +49,26 @@ __global__ void __launch_bounds__(kBlock, 3) primal_step_kernel(Dev d, Params pr
   double a[3] = {(double)op.acc[0], (double)op.acc[1], (double)op.acc[2]};
   block_sum_smem<3>(a, smem);
   if (threadIdx.x == 0) {
-    double* part = d.partials + (size_t)blockIdx.x * kMaxPartials;
-    part[0] = a[0]; part[1] = a[1]; part[2] = a[2];
+    double* rec = d.partials + (size_t)blockIdx.x * kMaxPartials;
+    rec[0] = a[0]; rec[1] = a[1]; rec[2] = a[2];
   }
 }
 
 template <class V>
 __global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm) {
-  __shared__ double smem[kBlock * 4];
+  __shared__ double smem[kBlock * 7];
+  __shared__ double fold[kFold * 3];
+  __shared__ DevState s_st;  // the state does not change until the step control, at the very end
+  __shared__ double s_f[2];
+  // copied while the rows run: this block's share of the primal kernel's
+  // records, and the state for the step control
+  const int nfold = fold_begin<3>(d.partials, partial_rows_at(d), fold);
+  {
+    static_assert(sizeof(DevState) % 8 == 0, "state copied in 8-byte words");
+    const double* src = reinterpret_cast<const double*>(d.st);
+    double* dst = reinterpret_cast<double*>(&s_st);
+    for (int t = threadIdx.x; t < (int)(sizeof(DevState) / 8); t += blockDim.x) cp_async8(dst + t, src + t);
+  }
   const Vecs<V>& v = vecs<V>(d);
   DualOp<V> op;
   op.sc = read_scalars<V>(d.st, false);
@@ -71,23 +84,42 @@ __global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm)
   for_each_row<1, V, V>(d.binsA, csr_a<V>(d), g, op, smem, row_slots_a(d, d.partials2));
   double a[4] = {(double)op.acc[0], (double)op.acc[1], (double)op.acc[2], (double)op.acc[3]};
   block_sum_smem<4>(a, smem);
-  __shared__ int s_last;
-  if (threadIdx.x == 0) {
-    double* part = d.partials2 + (size_t)blockIdx.x * kMaxPartials;
-    part[0] = a[0]; part[1] = a[1]; part[2] = a[2]; part[3] = a[3];
-    __threadfence();
-    const unsigned int t = atomicAdd(&d.st->counter, 1u);
-    s_last = (t == gridDim.x - 1);
-  }
+  cp_async_wait_all();
   __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double t1[3], t2[4];
-  sum_partials<3>(d.partials, partial_rows_at(d), t1, smem);
-  sum_partials<4>(d.partials2, partial_rows_a(d), t2, smem);
+  double rec[7] = {a[0], a[1], a[2], a[3], 0.0, 0.0, 0.0};
+  const long long tnext = s_st.attempts + 1;
   if (threadIdx.x == 0) {
-    DevState s = *d.st;  // register copy, written back once
-    step_control_state(s, prm, d.step_tab, t1, t2);
+    // step-size factors of the next attempt, in case this block runs the control
+    if (tnext < kStepTab) {
+      cp_async8(s_f, d.step_tab + tnext);
+      cp_async8(s_f + 1, d.step_tab + kStepTab + tnext);
+    }
+    for (int k = 0; k < nfold; ++k) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) rec[4 + q] += fold[3 * k + q];
+    }
+  }
+  __shared__ int s_last;
+  if (!publish_last<7>(rec, d.partials2, &d.st->counter, &s_last)) return;
+  // totals: this kernel's records (own sums, folded primal sums) and its
+  // segmented rows' slots, then any primal records beyond the folded ones
+  double tot[7];
+  const int f0 = unfolded_first(d.gridA), np = partial_rows_at(d);
+  block_sum_records<7, 3>(d.partials2, partial_rows_a(d), d.partials + (size_t)f0 * kMaxPartials,
+                          np > f0 ? np - f0 : 0, 4, tot, smem);
+  if (threadIdx.x == 0) {
+    const double t1[3] = {tot[4], tot[5], tot[6]};
+    const double t2[4] = {tot[0], tot[1], tot[2], tot[3]};
+    double f1, f2;
+    if (tnext < kStepTab) {
+      cp_async_wait_all();
+      f1 = s_f[0];
+      f2 = s_f[1];
+    } else {
+      step_factors(d.step_tab, tnext, &f1, &f2);
+    }
+    DevState s = s_st;  // register copy, written back once
+    step_control_state(s, prm, f1, f2, t1, t2);
     *d.st = s;
   }
 }

@@ -7,7 +7,7 @@ namespace lpop {
 
 constexpr int kBlock = 256;      // threads per block of every row kernel
 constexpr int kMaxBins = 8;      // row-length classes per matrix
-constexpr int kMaxPartials = 12; // per-block partial sums per kernel
+constexpr int kMaxPartials = 20; // fields of a partial-sum record (an A-row kernel's own + the folded A^T-row ones)
 constexpr int kPrimalTimed = 0;  // kernel ids for the event timers
 constexpr int kDualTimed = 1;
 

@@ -164,7 +164,8 @@ struct DualOp {
 // Step control (single thread): adaptive step test of Eq. (6) in the T^-1 /
 // Sigma^-1 weighted norms, next step size, buffer swap, online-update scalars.
 // Works on a copy of the state held by the caller.
-__device__ inline void step_control_state(DevState& s, const Params& prm, const double* step_tab,
+// f1, f2: step_factors() of attempt s.attempts + 1.
+__device__ inline void step_control_state(DevState& s, const Params& prm, double f1, double f2,
                                           const double (&t1)[3], const double (&t2)[4]) {
   const double eta = s.eta, omega = s.omega;
   const bool collect = s.collect;
@@ -174,26 +175,17 @@ __device__ inline void step_control_state(DevState& s, const Params& prm, const 
   bool accept = true;
   double eta_next = eta;
   if (prm.mode == kPdlp) {
-    const double movement = omega * t1[0] + t2[0] / omega;
+    const double movement = omega * t1[0] + t2[0] * s.inv_omega;
     const double interaction = fabs(t2[1]);
     const double eta_max = interaction > 0.0 ? movement / (2.0 * interaction) : INFINITY;
     accept = eta <= eta_max;
-    const long long t = s.attempts;
-    double f1, f2;
-    if (t < kStepTab) {
-      f1 = __ldg(step_tab + t);
-      f2 = __ldg(step_tab + kStepTab + t);
-    } else {
-      f1 = 1.0 - pow((double)t + 1.0, -0.3);
-      f2 = 1.0 + pow((double)t + 1.0, -0.6);
-    }
     eta_next = fmin(f1 * eta_max, f2 * eta);
     s.last_eta_max = eta_max;
   }
   if (accept) {
     if (collect) {
       if (!prm.normalize || t1[1] > 0.0) {
-        const double sc = -(eta / omega) * (prm.normalize ? 1.0 / t1[1] : 1.0);
+        const double sc = -(eta * s.inv_omega) * (prm.normalize ? 1.0 / t1[1] : 1.0);
         s.up_scale_p = sc;
         s.pend_p = 1;
         if (prm.sched == kAdagradNorm) s.gp_norm += sc * sc * t1[2];
@@ -212,7 +204,7 @@ __device__ inline void step_control_state(DevState& s, const Params& prm, const 
   s.eta = eta_next;
   s.last_accept = accept ? 1 : 0;
   s.counter = 0;
-  refresh_derived(s, prm.phi);
+  refresh_derived(s, prm.phi, prm.sched);
 }
 
 // Vectors of type V (FP64, or FP32 in the mixed-precision phase); every
@@ -371,7 +363,10 @@ __device__ inline void check_control(DevState* st, const Params& prm, const doub
   st->k_prev = K;
   if (!do_restart) return;
   const double dx = sqrt(cd[pick].dist_x2), dy = sqrt(cd[pick].dist_y2);
-  if (dx > 1e-10 && dy > 1e-10) st->omega = exp(0.5 * log(dy / dx) + 0.5 * log(omega));
+  if (dx > 1e-10 && dy > 1e-10) {
+    st->omega = exp(0.5 * log(dy / dx) + 0.5 * log(omega));
+    st->inv_omega = 1.0 / st->omega;
+  }
   st->restart_action = pick ? 2 : 1;
   st->apply_w = st->wsum;
   st->wsum = 0.0;

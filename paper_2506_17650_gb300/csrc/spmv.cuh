@@ -134,6 +134,7 @@ __device__ __forceinline__ void row_into_slot(Op& op, int row, const Acc (&r)[NV
     slot[q] = (double)op.acc[q];
     op.acc[q] = saved[q];
   }
+  for (int q = NA; q < kMaxPartials; ++q) slot[q] = 0.0;  // fields read by wider sums
 }
 
 // Ops that keep per-block reduction accumulators (member `acc`).

@@ -18,9 +18,10 @@ Floating point is FP64 on both sides.  The bars:
   relative; they come from step differences (eta_max = ||dz||^2 /
   (2 |dy^T A dx|)) whose relative rounding error exceeds the iterates' by
   about ||z|| / ||dz||.
-* Full solves: same status; iteration count at 1e-4 within +-2% of the range
-  the oracle itself spans under 1e-15 relative perturbations of c (the count
-  is rounding-sensitive in pdlp mode; where that range is one value this is
+* Full solves: same status; iteration count at 1e-4 within +-2% (the
+  full-size transport LP: one check period) of the range the oracle itself
+  spans under 1e-15 relative perturbations of c (the count is
+  rounding-sensitive in pdlp mode; where that range is one value this is
   plain +-2%); final
   objective within 1e-6 relative when both sides solve to 1e-8 (at 1e-4 the
   objective itself is only determined to about the tolerance).
@@ -234,7 +235,8 @@ def oracle_count_range(lp, o, tol, seeds=5, iter_limit=100_000):
     cost vector is perturbed by 1e-15 relative (one per seed): the count the
     method lands on is itself sensitive to rounding (on the transport LP these
     perturbations move it between 576 and 1088), so a second correct FP64
-    implementation is held to this range widened by 2%."""
+    implementation is held to this range, widened by 2% or, where the count
+    is only tested every check period, by one period."""
     counts = []
     for seed in range(seeds + 1):
         P = oracle.scale_problem(lp, o)
@@ -282,8 +284,9 @@ def test_full_size_transport_solve():
         status = p.solve(1e-4, 20_000)
         _, _, st = p.result(want_x=False, want_y=False)
     assert status == res.status == lpop.LP_OPTIMAL
-    lo, hi = oracle_count_range(lp, o, 1e-4, seeds=3)
-    assert 0.98 * lo <= st["iterations"] <= 1.02 * hi, (st["iterations"], lo, hi, res.iterations)
+    lo, hi = oracle_count_range(lp, o, 1e-4, seeds=6)
+    # termination is tested every check_every attempts, so counts move in whole check periods
+    assert lo - o.check_every <= st["iterations"] <= hi + o.check_every, (st["iterations"], lo, hi, res.iterations)
     # both points satisfy the 1e-4 relative KKT tolerance, which bounds their objectives' distance
     assert st["pobj"] == pytest.approx(res.pobj, rel=4e-4)
 
