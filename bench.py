@@ -452,23 +452,27 @@ def batch_arm(args):
     out = {}
     with lpop.Batch(probs) as b:
         tuned = b.autotune(TOL, 128)
-        for name, sched in (("fixed", (1, 1 << 62)), ("autotuned", tuned[:2])):
+        for name, sched, handoff in (("fixed", (1, 1 << 62), 0), ("autotuned", tuned[:2], 0),
+                                     ("autotuned_handoff", tuned[:2], args.batch_handoff)):
             b.set_schedule(*sched)
+            b.set_handoff(handoff)
             times = []
             launches = 0
             for rep in range(args.warmup + args.steps):
                 for p in probs:
                     p.reset()
                 torch.cuda.synchronize()
-                l0 = b.launches()
+                l0 = b.launches() + sum(p.kernel_times()[2] for p in probs)
                 t = time.perf_counter()
                 n_opt = b.solve(TOL, 200_000, 256)
                 torch.cuda.synchronize()
                 if rep >= args.warmup:
                     times.append(time.perf_counter() - t)
-                    launches += b.launches() - l0
+                    # batched rounds, state read-backs and the handed-off members' own kernels
+                    launches += b.launches() + sum(p.kernel_times()[2] for p in probs) - l0
             status, iters = b.status()
-            out[name] = {"schedule": {"cluster_size": int(sched[0]), "wide_nnz": int(min(sched[1], 1 << 62))},
+            out[name] = {"schedule": {"cluster_size": int(sched[0]), "wide_nnz": int(min(sched[1], 1 << 62)),
+                                      "handoff_attempts": int(handoff)},
                          "solve_s": statistics.median(times), "solves_per_s": count / statistics.median(times),
                          "optimal": int(n_opt), "iterations_sgm10": sgm10(iters),
                          "iterations_median": float(np.median(iters)), "iterations_max": int(iters.max()),
@@ -476,7 +480,7 @@ def batch_arm(args):
                          "gpu_launches": launches}
     for p in probs:
         p.close()
-    best = out["autotuned"]
+    best = max(out.values(), key=lambda r: r["solves_per_s"])
     line = {
         "metric": METRIC, "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * best["solve_s"], "higher_is_better": True, "scaling": "weak",
@@ -495,7 +499,9 @@ def batch_arm(args):
 def serve_arm(args):
     """Poisson arrivals of power-law LPs (nnz log-uniform [1e3, max]); the
     continuous-batching server against a one-LP-at-a-time FP64 loop on the
-    same request sequence."""
+    same request sequence.  Every request runs to relative KKT 1e-4 or to an
+    attempt cap (power-law LPs above ~1e5 nonzeros need far more than 5e4
+    attempts), and the report says how many reached the tolerance."""
     import numpy as np
     import torch
 
@@ -507,24 +513,24 @@ def serve_arm(args):
     lpbuild.build()
     torch.cuda.set_device(0)
     rng = np.random.default_rng(0)
-    count = args.serve_count
+    count, cap = args.serve_count, args.serve_attempts
     nnzs = np.floor(10 ** rng.uniform(3, np.log10(args.serve_max_nnz), size=count)).astype(int)
+    t0 = time.perf_counter()
     lps = []
     for i, z in enumerate(nnzs):
         n = max(int(z / 6), 20)
         m = max(int(0.4 * n), 8)
         lps.append(lpgen.powerlaw(20_000 + i, m, n, int(z), dmax=max(m // 4, 4)))
-    # warm the library (first launches, graph capture paths)
-    with lpop.Problem(lps[0], alpha=ALPHA, phi=PHI) as p:
-        p.solve(TOL, 20_000)
-    # service time of the sequential FP64 loop sets the arrival rate: load ~ rate x mean service
-    seq_t = []
-    seq_lat = []
+    gen_s = time.perf_counter() - t0
+    with lpop.Problem(lps[0], alpha=ALPHA, phi=PHI) as p:  # first launches, graph capture paths
+        p.solve(TOL, 2_000)
+    # one at a time, FP64: create, solve, read the result
+    seq_t, seq_opt = [], 0
     for lp in lps:
         torch.cuda.synchronize()
         t = time.perf_counter()
         with lpop.Problem(lp, alpha=ALPHA, phi=PHI) as p:
-            p.solve(TOL, 200_000)
+            seq_opt += p.solve(TOL, cap) == lpop.LP_OPTIMAL
             p.result()
         torch.cuda.synchronize()
         seq_t.append(time.perf_counter() - t)
@@ -533,19 +539,18 @@ def serve_arm(args):
     for load in args.serve_loads:
         rate = load / mean_service
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
-        # one at a time, FP64: a request waits for every earlier one
-        clock = 0.0
-        lat = []
-        for a, st in zip(arrivals, seq_t):
+        clock, lat = 0.0, []
+        for a, st in zip(arrivals, seq_t):  # FIFO, a request waits for every earlier one
             clock = max(clock, a) + st
             lat.append(clock - a)
         seq = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-               "solves_per_s": count / (clock - arrivals[0] + seq_t[0])}
-        srv = Server(tol=TOL, round_attempts=128, alpha=ALPHA, phi=PHI)
+               "solves_per_s": count / (clock - arrivals[0]), "reached_tol": int(seq_opt)}
+        srv = Server(tol=TOL, iter_limit=cap, round_attempts=128, alpha=ALPHA, phi=PHI,
+                     solo_nnz=args.serve_solo_nnz, handoff=args.batch_handoff)
         start = time.perf_counter()
         srv.clock = lambda: time.perf_counter() - start
         nxt = 0
-        while nxt < count or srv.active or srv.queue:
+        while nxt < count or srv.active or srv.queue or srv.solo:
             now = srv.clock()
             while nxt < count and arrivals[nxt] <= now:
                 srv.submit(lps[nxt], arrival=float(arrivals[nxt]))
@@ -557,15 +562,18 @@ def serve_arm(args):
         srv.close()
         results[f"load_{load}"] = {"arrival_rate_per_s": rate, "server": dict(rep, solves_per_s=count / span),
                                    "one_at_a_time_fp64": seq}
+    last = results[f"load_{args.serve_loads[-1]}"]
     line = {
-        "metric": METRIC, "value": results[f"load_{args.serve_loads[-1]}"]["server"]["solves_per_s"],
-        "unit": "solves/s", "n_gpus": 1, "steps": count, "warmup": 1, "higher_is_better": True,
+        "metric": METRIC, "value": last["server"]["solves_per_s"], "unit": "requests/s", "n_gpus": 1,
+        "steps": count, "warmup": 1, "ms_per_step": 1e3 / last["server"]["solves_per_s"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 products/updates, f64 reductions and refinement",
         "data": "synthetic",
         "config": {"workload": f"{count} power-law LPs, nnz log-uniform [1e3, {args.serve_max_nnz:g}], n = nnz/6, "
-                               "m = 0.4 n, Poisson arrivals at load x (1 / mean FP64 service time)",
-                   "tol": TOL, "loads": list(args.serve_loads)},
-        "serving": results, "mean_fp64_service_s": mean_service,
+                               "m = 0.4 n, Poisson arrivals at load x (1 / mean one-at-a-time FP64 service time)",
+                   "tol": TOL, "attempt_cap": cap, "loads": list(args.serve_loads),
+                   "solo_nnz": args.serve_solo_nnz, "handoff_attempts": args.batch_handoff},
+        "serving": results, "mean_fp64_service_s": mean_service, "generation_s": gen_s,
+        "request_nnz": [int(lp.nnz) for lp in lps],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -606,9 +614,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="transport", choices=["transport", "powerlaw", "batch", "serve"])
     ap.add_argument("--batch-count", type=int, default=512)
-    ap.add_argument("--serve-count", type=int, default=48)
-    ap.add_argument("--serve-max-nnz", type=float, default=1e6)
+    ap.add_argument("--batch-handoff", type=int, default=2048,
+                    help="attempts after which a batch member finishes on the single-problem kernels")
+    ap.add_argument("--serve-count", type=int, default=24)
+    ap.add_argument("--serve-max-nnz", type=float, default=1e7)
     ap.add_argument("--serve-loads", type=float, nargs="+", default=[0.5, 2.0])
+    ap.add_argument("--serve-attempts", type=int, default=10_000, help="attempt cap per request")
+    ap.add_argument("--serve-solo-nnz", type=int, default=200_000,
+                    help="requests with at least this many nonzeros run on the single-problem kernels")
     ap.add_argument("--scale", type=float, default=1.0, help="size factor of the power-law workload")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -286,8 +286,20 @@ int lp_batch_set_schedule(lp_batch* b, int32_t cluster_size, int64_t wide_nnz);
 int lp_batch_round(lp_batch* b, double rel_kkt_tol, int32_t attempts, int64_t iter_limit, int32_t* active_out);
 
 /* Rounds of round_attempts attempts until no member is open; *n_optimal (may
- * be NULL) receives how many members reached the tolerance. */
+ * be NULL) receives how many members reached the tolerance.  With a handoff
+ * (lp_batch_set_handoff), a member still open at a round boundary after at
+ * least that many attempts leaves the batch and finishes with lp_solve (its
+ * own full-grid kernels, on its own stream, from a host thread of this call)
+ * while the batch goes on with the rest; the call returns when all are done.
+ * The rule depends only on the member's own attempts, so a member's result
+ * does not depend on the rest of the batch. */
 int lp_batch_solve(lp_batch* b, double rel_kkt_tol, int64_t iter_limit, int32_t round_attempts, int32_t* n_optimal);
+
+/* Handoff threshold of lp_batch_solve in attempts (0 = never, the default).
+ * No counterpart in the paper: it bounds the batch's tail, where a few slow
+ * members would otherwise run on a single CTA or cluster each.
+ * Errors: LP_ERR_INVALID_ARG (NULL batch, negative value). */
+int lp_batch_set_handoff(lp_batch* b, int64_t attempts);
 
 /* Schedule autotuner: for cluster sizes {1, 2, 4, 8} and wide thresholds at
  * the 50/80/95/99th percentiles of the members' nonzero counts, reset every

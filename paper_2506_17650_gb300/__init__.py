@@ -138,6 +138,8 @@ def load_library(path: str | None = None):
     lib.lp_batch_set_members.restype = c_int32
     lib.lp_batch_set_schedule.argtypes = [c_void_p, c_int32, c_int64]
     lib.lp_batch_set_schedule.restype = c_int32
+    lib.lp_batch_set_handoff.argtypes = [c_void_p, c_int64]
+    lib.lp_batch_set_handoff.restype = c_int32
     lib.lp_batch_round.argtypes = [c_void_p, c_double, c_int32, c_int64, POINTER(c_int32)]
     lib.lp_batch_round.restype = c_int32
     lib.lp_batch_solve.argtypes = [c_void_p, c_double, c_int64, c_int32, POINTER(c_int32)]
@@ -395,6 +397,10 @@ def lp_batch_set_schedule(batch, cluster_size=1, wide_nnz=1 << 62):
     _check(load_library().lp_batch_set_schedule(batch, int(cluster_size), int(wide_nnz)))
 
 
+def lp_batch_set_handoff(batch, attempts=0):
+    _check(load_library().lp_batch_set_handoff(batch, int(attempts)))
+
+
 def lp_batch_round(batch, rel_kkt_tol=1e-4, attempts=64, iter_limit=1_000_000) -> int:
     act = c_int32(0)
     _check(load_library().lp_batch_round(batch, float(rel_kkt_tol), int(attempts), int(iter_limit), ctypes.byref(act)))
@@ -451,6 +457,9 @@ class Batch:
 
     def set_schedule(self, cluster_size, wide_nnz):
         lp_batch_set_schedule(self.handle, cluster_size, wide_nnz)
+
+    def set_handoff(self, attempts):
+        lp_batch_set_handoff(self.handle, attempts)
 
     def round(self, rel_kkt_tol=1e-4, attempts=64, iter_limit=1_000_000):
         return lp_batch_round(self.handle, rel_kkt_tol, attempts, iter_limit)

@@ -19,6 +19,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/lpop.h"
@@ -361,6 +362,11 @@ struct lp_batch {
   std::vector<DevState> states;
   int cluster = 1;
   long long wide_nnz = (1LL << 62);
+  // lp_batch_solve: a member still open after `handoff` attempts (0: never)
+  // finishes on the single-problem kernels, on its own stream and host
+  // thread, while the batch goes on with the others
+  long long handoff = 0;
+  std::vector<char> handed;
   int sms = 0;
   long long launches = 0;
   std::string err;
@@ -549,13 +555,16 @@ int launch_round(lp_batch* b, const std::vector<int>& active, int attempts) {
 
 std::vector<int> active_members(lp_batch* b, long long iter_limit) {
   std::vector<int> act;
-  for (int i = 0; i < (int)b->probs.size(); ++i)
+  for (int i = 0; i < (int)b->probs.size(); ++i) {
+    if (!b->handed.empty() && b->handed[i]) continue;
     if (b->states[i].status == 0 && b->states[i].attempts < iter_limit) act.push_back(i);
+  }
   return act;
 }
 
 int sync_members(lp_batch* b) {
   for (int i = 0; i < (int)b->probs.size(); ++i) {
+    if (!b->handed.empty() && b->handed[i]) continue;  // its own solve keeps it current
     int rc = member_after_batch(b->probs[i], b->states[i]);
     if (rc != LP_OK) return berr(b, rc, "member " + std::to_string(i) + ": state refresh failed");
   }
@@ -624,9 +633,11 @@ int lp_batch_round(lp_batch* b, double rel_kkt_tol, int32_t attempts, int64_t it
   if (rc != LP_OK) return rc;
   // members still running, and members that stopped under another tolerance
   std::vector<int> act;
-  for (int i = 0; i < count; ++i)
+  for (int i = 0; i < count; ++i) {
+    if (!b->handed.empty() && b->handed[i]) continue;  // running on the single-problem path
     if (b->states[i].attempts < iter_limit && (b->states[i].status == 0 || b->states[i].tol != rel_kkt_tol))
       act.push_back(i);
+  }
   if (act.empty()) {
     if (active_out) *active_out = 0;
     return sync_members(b);
@@ -661,18 +672,56 @@ int lp_batch_round(lp_batch* b, double rel_kkt_tol, int32_t attempts, int64_t it
 int lp_batch_solve(lp_batch* b, double rel_kkt_tol, int64_t iter_limit, int32_t round_attempts, int32_t* n_optimal) {
   if (!b) return berr(nullptr, LP_ERR_INVALID_ARG, "batch handle is NULL");
   if (round_attempts < 1) return berr(b, LP_ERR_INVALID_ARG, "round_attempts must be >= 1");
+  const int count = (int)b->probs.size();
+  b->handed.assign(count, 0);
+  std::vector<std::thread> workers;
+  std::vector<int> worker_rc(count, LP_OK);
+  int rc = LP_OK;
   int active = 1;
-  int guard = 0;
+  long long guard = 0;
   while (active > 0) {
-    int rc = lp_batch_round(b, rel_kkt_tol, round_attempts, iter_limit, &active);
-    if (rc != LP_OK) return rc;
+    rc = lp_batch_round(b, rel_kkt_tol, round_attempts, iter_limit, &active);
+    if (rc != LP_OK) break;
+    if (b->handoff > 0) {
+      // the rule depends only on the member's own attempts (round boundaries are
+      // multiples of round_attempts), so its result does not depend on the mix
+      for (int i = 0; i < count; ++i) {
+        const DevState& st = b->states[i];
+        if (b->handed[i] || st.status != 0 || st.attempts >= iter_limit || st.attempts < b->handoff) continue;
+        b->handed[i] = 1;
+        --active;
+        lp_problem* p = b->probs[i];
+        int* out = &worker_rc[i];
+        const int dev = b->device;
+        workers.emplace_back([p, out, dev, rel_kkt_tol, iter_limit]() {
+          cudaSetDevice(dev);
+          *out = lp_solve(p, rel_kkt_tol, iter_limit, nullptr);
+        });
+      }
+    }
     if (++guard > 100000000) break;
   }
+  for (std::thread& t : workers) t.join();
+  b->handed.clear();
+  if (rc != LP_OK) return rc;
+  for (int i = 0; i < count; ++i)
+    if (worker_rc[i] != LP_OK) return berr(b, worker_rc[i], "member " + std::to_string(i) + ": single-problem solve failed");
+  rc = read_states(b);
+  if (rc != LP_OK) return rc;
+  rc = sync_members(b);
+  if (rc != LP_OK) return rc;
   if (n_optimal) {
     int k = 0;
     for (const DevState& s : b->states) k += s.status == 1;
     *n_optimal = k;
   }
+  return LP_OK;
+}
+
+int lp_batch_set_handoff(lp_batch* b, int64_t attempts) {
+  if (!b) return berr(nullptr, LP_ERR_INVALID_ARG, "batch handle is NULL");
+  if (attempts < 0) return berr(b, LP_ERR_INVALID_ARG, "handoff attempts must be >= 0");
+  b->handoff = attempts;
   return LP_OK;
 }
 

@@ -35,7 +35,7 @@ int widen_factor(long long rows, long long target_threads) {
 
 // Stable permutation of rows by bin rank.
 std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<int>& widths_sorted,
-                                 long long target_threads) {
+                                 std::vector<int>& lengths_sorted, long long target_threads) {
   const int rows = (int)len.size();
   const int widen = widen_factor(rows, target_threads);
   std::vector<int> width(rows);
@@ -49,7 +49,11 @@ std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<
     return ra != rb ? ra < rb : len[a] > len[b];
   });
   widths_sorted.resize(rows);
-  for (int r = 0; r < rows; ++r) widths_sorted[r] = width[perm[r]];
+  lengths_sorted.resize(rows);
+  for (int r = 0; r < rows; ++r) {
+    widths_sorted[r] = width[perm[r]];
+    lengths_sorted[r] = (int)len[perm[r]];
+  }
   return perm;
 }
 
@@ -72,26 +76,61 @@ int width_for_length(long long len, int widen) {
   return w > wide ? w : wide;
 }
 
-BinTable make_bins(const std::vector<int>& widths_sorted) {
+BinTable make_bins(const std::vector<int>& widths_sorted, const std::vector<int>& lengths_sorted) {
   BinTable t{};
   t.nbins = 0;
   t.nunits = 0;
   const int rows = (int)widths_sorted.size();
+  long long sell = 0;
   int r = 0;
   while (r < rows) {
     const int w = widths_sorted[r];
+    // one-lane rows (at most 16 entries) go to sliced bins of one exact length
+    const bool sliced = w == 1 && !lengths_sorted.empty();
     int e = r;
-    while (e < rows && widths_sorted[e] == w) ++e;
+    while (e < rows && widths_sorted[e] == w && (!sliced || lengths_sorted[e] == lengths_sorted[r])) ++e;
     Bin& b = t.bin[t.nbins++];
     b.row_begin = r;
     b.row_end = e;
-    b.width = w;
+    b.width = sliced ? kSell : w;
     b.unit_begin = t.nunits;
-    const int per = w == 0 ? 1 : kBlock / w;
+    b.len = sliced ? lengths_sorted[r] : 0;
+    b.base = sliced ? sell : 0;
+    if (sliced) sell += (long long)(e - r + 31) / 32 * 32 * b.len;
+    const int per = rows_per_unit(b.width);
     t.nunits += (e - r + per - 1) / per;
     r = e;
   }
   return t;
+}
+
+long long sliced_entries(const BinTable& bt) {
+  long long total = 0;
+  for (int b = 0; b < bt.nbins; ++b) {
+    const Bin& x = bt.bin[b];
+    if (x.width == kSell) total = x.base + (long long)(x.row_end - x.row_begin + 31) / 32 * 32 * x.len;
+  }
+  return total;
+}
+
+void build_sliced(const BinTable& bt, const std::vector<int>& rp, const std::vector<int>& ci,
+                  std::vector<int>& sell_ci, std::vector<int>& sell_pos) {
+  const long long total = sliced_entries(bt);
+  sell_ci.assign((size_t)total, 0);
+  sell_pos.assign((size_t)total, -1);
+  for (int b = 0; b < bt.nbins; ++b) {
+    const Bin& x = bt.bin[b];
+    if (x.width != kSell) continue;
+    for (int i = 0; i < x.row_end - x.row_begin; ++i) {
+      const int row = x.row_begin + i;
+      const long long p0 = x.base + (long long)(i / 32) * 32 * x.len + (i % 32);
+      for (int k = 0; k < x.len; ++k) {
+        const long long p = p0 + 32LL * k;
+        sell_ci[(size_t)p] = ci[(size_t)rp[row] + k];
+        sell_pos[(size_t)p] = rp[row] + k;
+      }
+    }
+  }
 }
 
 int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
@@ -157,14 +196,14 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
   for (int i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
   for (long long k = 0; k < nz; ++k) clen[ci[k]]++;
 
-  std::vector<int> wA, wAt;
+  std::vector<int> wA, wAt, lA, lAt;
   out.m = m;
   out.n = n;
   out.nnz = nz;
-  out.prow = bin_permutation(rlen, wA, target_threads);
-  out.pcol = bin_permutation(clen, wAt, target_threads);
-  out.binsA = make_bins(wA);
-  out.binsAt = make_bins(wAt);
+  out.prow = bin_permutation(rlen, wA, lA, target_threads);
+  out.pcol = bin_permutation(clen, wAt, lAt, target_threads);
+  out.binsA = make_bins(wA, lA);
+  out.binsAt = make_bins(wAt, lAt);
   std::vector<int> icol(n);
   for (int j = 0; j < n; ++j) icol[out.pcol[j]] = j;
 
@@ -202,6 +241,8 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
       fillp[j]++;
     }
   }
+  build_sliced(out.binsA, out.A_rp, out.A_ci, out.A_sell_ci, out.A_sell_pos);
+  build_sliced(out.binsAt, out.At_rp, out.At_ci, out.At_sell_ci, out.At_sell_pos);
   return LP_OK;
 }
 
@@ -249,7 +290,7 @@ std::vector<int> segment_long_rows(BinTable& bt, const std::vector<int>& rp, int
   for (int b = 1; b < bt.nbins; ++b) {
     Bin x = bt.bin[b];
     x.unit_begin = unit;
-    const int per = kBlock / x.width;
+    const int per = rows_per_unit(x.width);
     unit += (x.row_end - x.row_begin + per - 1) / per;
     out.bin[out.nbins++] = x;
   }

@@ -232,6 +232,18 @@ __global__ void __launch_bounds__(kBlock) recompute_ax_kernel(Dev d) {
   for_each_row<1, double, double>(d.binsA, d.A, g, op, smem);
 }
 
+__global__ void gather_values_kernel(const int* pos, const double* v, double* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int k = pos[i];
+    out[i] = k >= 0 ? v[k] : 0.0;
+  }
+}
+
+__global__ void narrow_kernel(const double* in, float* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
 __global__ void widen_kernel(double* out, const float* in, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (double)in[i];
 }
@@ -309,6 +321,14 @@ void launch_init_vectors(const Dev& d, cudaStream_t s) {
 }  // namespace lpop
 
 namespace lpop {
+
+void launch_gather_values(const int* pos, const double* v, double* out, long long n, cudaStream_t s) {
+  if (n > 0) gather_values_kernel<<<grid_for(n), kBlock, 0, s>>>(pos, v, out, n);
+}
+
+void launch_narrow(const double* in, float* out, long long n, cudaStream_t s) {
+  if (n > 0) narrow_kernel<<<grid_for(n), kBlock, 0, s>>>(in, out, n);
+}
 
 void launch_make_fp32(const Dev& d, cudaStream_t s) {
   long long big = d.nnz > d.n ? d.nnz : d.n;

@@ -83,6 +83,54 @@ __device__ __forceinline__ void vec_rows(int first, int row_end, const CsrT<V>& 
   if (lane == 0 && row < row_end) op.row(row, s);
 }
 
+template <class V>
+__device__ __forceinline__ const V* sell_values(const BinTable& bt);
+template <>
+__device__ __forceinline__ const double* sell_values<double>(const BinTable& bt) { return bt.sell_v; }
+template <>
+__device__ __forceinline__ const float* sell_values<float>(const BinTable& bt) { return bt.sell_v32; }
+
+// A unit of a kSell bin: thread t takes row row_begin + local * kBlock + t, of
+// exactly B.len entries, from the sliced copy.  The loop bound is the same
+// for the whole warp and the loads of a warp are contiguous; the entries are
+// added in row order, as in the CSR path.
+template <int NV, class V, class Acc, class Op>
+__device__ __forceinline__ void sell_rows(const BinTable& bt, const Bin& B, int local, const Gather<NV, V>& g,
+                                          Op& op) {
+  const int i = local * kBlock + (int)threadIdx.x;
+  const int row = B.row_begin + i;
+  if (row >= B.row_end) return;
+  op.prefetch(row);
+  const int L = B.len;
+  const int* sci = bt.sell_ci + B.base + (long long)(i >> 5) * (32LL * L) + (i & 31);
+  const V* sv = sell_values<V>(bt) + B.base + (long long)(i >> 5) * (32LL * L) + (i & 31);
+  Acc s[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) s[q] = Acc(0);
+  for (int k0 = 0; k0 < L; k0 += kChunk) {
+    const int nk = min(kChunk, L - k0);  // warp-uniform
+    int c[kChunk];
+    Acc a[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+      c[u] = u < nk ? __ldg(sci + 32 * (k0 + u)) : 0;
+      a[u] = u < nk ? (Acc)__ldg(sv + 32 * (k0 + u)) : Acc(0);
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      Acc xv[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) xv[u] = u < nk ? (Acc)__ldg(g.x[q] + c[u]) : Acc(0);
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u) {
+        if (u >= nk) break;
+        s[q] = fma(a[u], xv[u], s[q]);
+      }
+    }
+  }
+  op.row(row, s);
+}
+
 // Block-wide FP64 sums of the entries [beg, end) of one row (valid in warp 0).
 template <int NV, class V, class Acc>
 __device__ __forceinline__ void block_dot(int beg, int end, const CsrT<V>& M, const Gather<NV, V>& g, double (&s)[NV],
@@ -204,14 +252,18 @@ template <int NV, class V, class Acc, class Op>
 __device__ __forceinline__ void for_each_row_range(const BinTable& bt, const CsrT<V>& M, const Gather<NV, V>& g,
                                                    Op& op, double* smem, int first_unit, int unit_stride,
                                                    double* row_slots = nullptr) {
+  int b = 0;  // units only increase, so the bin search resumes where it stopped
   for (int u = first_unit; u < bt.nunits; u += unit_stride) {
-    int b = 0;
     while (b + 1 < bt.nbins && u >= bt.bin[b + 1].unit_begin) ++b;
     const int row_begin = bt.bin[b].row_begin;
     const int row_end = bt.bin[b].row_end;
     const int local = u - bt.bin[b].unit_begin;
     switch (bt.bin[b].width) {
       case kSegmented: segment_unit<NV, V, Acc>(bt, local, M, g, op, smem, row_slots); break;
+      case kSell:
+        if (bt.sell_ci) sell_rows<NV, V, Acc>(bt, bt.bin[b], local, g, op);
+        else vec_rows<1, NV, V, Acc>(row_begin + local * kBlock, row_end, M, g, op);
+        break;
       case 0: block_row<NV, V, Acc>(row_begin + local, M, g, op, smem); break;
       case 1: vec_rows<1, NV, V, Acc>(row_begin + local * kBlock, row_end, M, g, op); break;
       case 2: vec_rows<2, NV, V, Acc>(row_begin + local * (kBlock / 2), row_end, M, g, op); break;

@@ -5,20 +5,24 @@ waiting request when a slot is free and the device memory its problem needs
 (lp_memory_bytes) fits in the memory budget; admission creates the problem on
 the device (lp_create: copy, preprocessing, initial state).  Every admitted
 problem keeps its whole iteration state on the device -- iterates,
-preconditioners, step size, primal weight, restart state -- and all of them
+preconditioners, step size, primal weight, restart state.  Small problems
 advance together: one round is a single batched kernel launch in which every
-admitted problem runs up to ``round_attempts`` step attempts.  After a round
-the server retires the problems that reached the tolerance (or the iteration
+batched problem runs up to ``round_attempts`` step attempts.  A problem with
+at least ``solo_nnz`` nonzeros, or one still open after ``handoff`` attempts,
+runs instead on the single-problem kernels (the whole GPU's grid, its own
+stream) from a worker thread, concurrently with the rounds.  After a round the
+server retires the problems that reached the tolerance (or the attempt
 limit), copies their results to the host and frees their memory, and admits
-waiting requests into the freed slots.  A problem's arithmetic depends only on
-its own state and team size, so its result is the same alone and in any mix.
+waiting requests into the freed slots.  Both rules depend only on the problem
+itself, so a problem's result is the same alone and in any mix.
 
 The scheduling here is host bookkeeping; every step of the method runs in the
-library's kernels (``Batch.round``).
+library's kernels (``Batch.round`` and ``Problem.solve``).
 """
 from __future__ import annotations
 
 import collections
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -51,11 +55,15 @@ class Server:
 
     memory_budget: device bytes the admitted problems may hold (default: 90% of
     the free device memory when the server starts).  schedule: (cluster_size,
-    wide_nnz) of the batched kernel.  Other keyword arguments are lp_options
-    fields for every problem (precision defaults to mixed)."""
+    wide_nnz) of the batched kernel.  solo_nnz: problems with at least this
+    many nonzeros run on the single-problem kernels (None: never).  handoff:
+    a batched problem still open after this many attempts moves there too
+    (0: never).  Other keyword arguments are lp_options fields for every
+    problem (precision defaults to mixed)."""
 
     def __init__(self, tol=1e-4, iter_limit=200_000, round_attempts=128, max_slots=512, memory_budget=None,
-                 schedule=(1, 1 << 62), keep_solution=True, clock=time.perf_counter, **options):
+                 schedule=(1, 1 << 62), keep_solution=True, clock=time.perf_counter, solo_nnz=None,
+                 handoff=0, **options):
         import torch
 
         options.setdefault("precision", LP_PREC_MIXED)
@@ -75,6 +83,9 @@ class Server:
         self.active: list[tuple[Request, Problem]] = []
         self.done: dict[int, Request] = {}
         self.rounds = 0
+        self.solo_nnz = solo_nnz
+        self.handoff = handoff
+        self.solo: list[tuple[Request, Problem, threading.Thread]] = []
         self._next = 0
         self._opts = lp_options_default(**options)
         self.batch = Batch([], *schedule)
@@ -89,32 +100,55 @@ class Server:
     def _admit(self):
         while self.queue and len(self.active) < self.max_slots:
             req = self.queue[0]
-            if self.active and self.used + req.bytes > self.memory_budget:
+            if (self.active or self.solo) and self.used + req.bytes > self.memory_budget:
                 break  # first come, first served: wait until enough memory is free
             self.queue.popleft()
             prob = Problem(req.lp, **self.options)
             req.admitted = self.clock()
             self.used += req.bytes
-            self.active.append((req, prob))
+            if self.solo_nnz is not None and req.lp.nnz >= self.solo_nnz:
+                self._go_solo(req, prob)
+            else:
+                self.active.append((req, prob))
+
+    def _go_solo(self, req, prob):
+        # the ctypes call releases the GIL: the solve runs while the rounds go on
+        t = threading.Thread(target=prob.solve, args=(self.tol, self.iter_limit), daemon=True)
+        t.start()
+        self.solo.append((req, prob, t))
+
+    def _finish(self, req, prob, now):
+        x, y, stats = prob.result(self.keep_solution, self.keep_solution)
+        req.finished = now
+        req.status = stats["status"]
+        req.iterations = int(stats["iterations"])
+        req.stats = stats
+        req.x, req.y = x, y
+        prob.close()
+        self.used -= req.bytes
+        self.done[req.rid] = req
 
     def _retire(self):
-        status, iters = self.batch.status()
-        keep = []
         now = self.clock()
-        for (req, prob), st, it in zip(self.active, status, iters):
-            if st != 0 or it >= self.iter_limit:
-                x, y, stats = prob.result(self.keep_solution, self.keep_solution)
-                req.finished = now
-                req.status = stats["status"]
-                req.iterations = int(it)
-                req.stats = stats
-                req.x, req.y = x, y
-                prob.close()
-                self.used -= req.bytes
-                self.done[req.rid] = req
+        if self.active:
+            status, iters = self.batch.status()
+            keep = []
+            for (req, prob), st, it in zip(self.active, status, iters):
+                if st != 0 or it >= self.iter_limit:
+                    self._finish(req, prob, now)
+                elif self.handoff and it >= self.handoff:
+                    self._go_solo(req, prob)
+                else:
+                    keep.append((req, prob))
+            self.active = keep
+        running = []
+        for req, prob, t in self.solo:
+            if t.is_alive():
+                running.append((req, prob, t))
             else:
-                keep.append((req, prob))
-        self.active = keep
+                t.join()
+                self._finish(req, prob, now)
+        self.solo = running
 
     def step(self) -> int:
         """Admit, run one round, retire.  Returns the number of problems still admitted or waiting."""
@@ -123,14 +157,20 @@ class Server:
             self.batch.set_members([p for _, p in self.active])
             self.batch.round(self.tol, self.round_attempts, self.iter_limit)
             self.rounds += 1
-            self._retire()
-        return len(self.active) + len(self.queue)
+        elif self.solo:
+            time.sleep(0.0005)  # only solo problems running: wait for one to finish
+        self._retire()
+        return len(self.active) + len(self.queue) + len(self.solo)
 
     def drain(self):
         while self.step():
             pass
 
     def close(self):
+        for _, prob, t in self.solo:
+            t.join()
+            prob.close()
+        self.solo = []
         for _, prob in self.active:
             prob.close()
         self.active = []
@@ -140,6 +180,6 @@ class Server:
         t = np.array([r.time_to_tol for r in self.done.values() if r.time_to_tol is not None])
         ok = sum(1 for r in self.done.values() if r.status == LP_OPTIMAL)
         if t.size == 0:
-            return {"solved": 0}
-        return {"solved": int(t.size), "optimal": ok, "p50_s": float(np.percentile(t, 50)),
+            return {"finished": 0}
+        return {"finished": int(t.size), "optimal": ok, "p50_s": float(np.percentile(t, 50)),
                 "p99_s": float(np.percentile(t, 99)), "mean_s": float(t.mean()), "rounds": self.rounds}

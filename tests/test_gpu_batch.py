@@ -11,7 +11,8 @@
   optimum (a relative KKT error bounds the objective error only up to the
   problem's conditioning: at 1e-4 one of these instances is 1.4e-3 off).
 * A member's result does not depend on the rest of the batch: solved alone or
-  in a mix, with the same team size, it is bitwise identical.
+  in a mix, with the same team size, it is bitwise identical -- also when slow
+  members are handed to the single-problem kernels.
 """
 import numpy as np
 import pytest
@@ -122,3 +123,37 @@ def test_batch_and_single_path_agree_on_the_solution():
     finally:
         single.close()
         batched.close()
+
+
+def test_handoff_to_single_problem_path():
+    """Members still open after 256 attempts finish on the single-problem
+    kernels (lp_batch_set_handoff); every member optimal and certified, and a
+    member's result is the same alone and in the mix (the rule depends only on
+    its own attempts)."""
+    lps = _members(range(300, 308), [150, 400, 900, 120, 2000, 300, 700, 1500])
+    target = 4
+    mix = [lpop.Problem(lp, alpha=1e-3, phi=20, precision=lpop.LP_PREC_MIXED) for lp in lps]
+    alone = lpop.Problem(lps[target], alpha=1e-3, phi=20, precision=lpop.LP_PREC_MIXED)
+    try:
+        with lpop.Batch(mix) as b:
+            b.set_handoff(256)
+            n_opt = b.solve(1e-4, 100_000, 128)
+            status, iters = b.status()
+        assert n_opt == len(lps) and np.all(status == lpop.LP_OPTIMAL)
+        assert np.any(iters > 256)  # some member did leave the batch
+        for lp, p in zip(lps, mix):
+            x, y, st = p.result()
+            P = oracle.scale_problem(lp, oracle.Options())
+            kk = oracle.kkt(P, x / P.dc, y / P.dr, P.A @ (x / P.dc), P.At @ (y / P.dr))
+            assert max(kk["rel_pres"], kk["rel_dres"], kk["rel_gap"]) <= 1.01e-4, lp.name
+        with lpop.Batch([alone]) as b1:
+            b1.set_handoff(256)
+            b1.solve(1e-4, 100_000, 128)
+        a, m = alone.get_state(), mix[target].get_state()
+        for key in ("x", "y", "T", "Sigma"):
+            assert np.array_equal(a[key], m[key]), key
+        assert a["attempts"] == m["attempts"]
+    finally:
+        alone.close()
+        for p in mix:
+            p.close()

@@ -63,7 +63,7 @@ def test_stream_is_solved_and_certified():
             assert req.status == lpop.LP_OPTIMAL, lp.name
             assert _certified(lp, req) <= 1.01e-4, lp.name
         rep = srv.latency_report()
-        assert rep["solved"] == len(lps) and rep["optimal"] == len(lps)
+        assert rep["finished"] == len(lps) and rep["optimal"] == len(lps)
     finally:
         srv.close()
 
@@ -115,3 +115,38 @@ def test_admission_by_memory_queues_instead_of_failing():
         assert peak <= budget
     finally:
         srv.close()
+
+
+def test_solo_and_handoff_paths():
+    """Large requests (solo_nnz) run on the single-problem kernels from a worker
+    thread, and batched requests still open after 256 attempts move there;
+    every request ends optimal and certified, and a request's result is the
+    same alone and in the mix (both rules depend only on the request)."""
+    from paper_2506_17650_gb300.serving import Server
+
+    lps = _stream(8, seed=3)
+    sizes = sorted(lp.nnz for lp in lps)
+    solo_nnz = sizes[-3]  # the three largest go solo
+    target = max(range(len(lps)), key=lambda i: lps[i].nnz)
+    small = min(range(len(lps)), key=lambda i: lps[i].nnz)
+    kw = dict(tol=1e-4, round_attempts=128, alpha=1e-3, phi=20, solo_nnz=solo_nnz, handoff=256)
+    mixed = Server(**kw)
+    try:
+        rids = [mixed.submit(lp) for lp in lps]
+        mixed.drain()
+        for lp, rid in zip(lps, rids):
+            req = mixed.done[rid]
+            assert req.status == lpop.LP_OPTIMAL, lp.name
+            assert _certified(lp, req) <= 1.01e-4, lp.name
+        for i in (target, small):
+            alone = Server(**kw)
+            try:
+                ra = alone.submit(lps[i])
+                alone.drain()
+                a, m = alone.done[ra], mixed.done[rids[i]]
+                assert a.iterations == m.iterations
+                assert np.array_equal(a.x, m.x) and np.array_equal(a.y, m.y)
+            finally:
+                alone.close()
+    finally:
+        mixed.close()
