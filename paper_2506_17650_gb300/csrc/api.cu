@@ -571,6 +571,7 @@ int set_state_impl(lp_problem* p, const double* vn, const double* vm, const doub
   hs.klast_g2 = scal[7];
   hs.k_prev = scal[8];
   hs.k = (long long)scal[9];
+  hs.k_mod = p->prm.phi > 0 ? (int)(hs.k % p->prm.phi) : 0;
   hs.attempts = (long long)scal[10];
   hs.last_restart_attempt = (long long)scal[11];
   hs.restarts = (long long)scal[12];

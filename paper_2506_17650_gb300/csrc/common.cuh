@@ -56,6 +56,7 @@ struct DevState {
   int cur;        // which half of the double buffers holds the current iterate
   int status;     // 0 running, 1 optimal, 4 numerical error
   long long k;    // accepted steps
+  int k_mod;      // k mod phi (kept with k: no 64-bit division in the step control)
   long long attempts;
   double eta;
   double omega;
@@ -107,7 +108,7 @@ constexpr int kStepTab = 1 << 20;
 // a long dependent chain on GB300: 1/omega is kept with omega, and the
 // square roots are taken only for the scheduler that uses them.
 __host__ __device__ inline void refresh_derived(DevState& s, int phi, int sched) {
-  s.collect = phi > 0 && (s.k % phi) == 0;
+  s.collect = phi > 0 && s.k_mod == 0;
   s.step_p = s.eta * s.inv_omega;
   s.step_d = s.eta * s.omega;
   const bool norm = sched == kAdagradNorm;
@@ -285,17 +286,20 @@ __device__ inline int fold_begin(const double* rec, int count, double* fold) {
 __host__ __device__ inline int unfolded_first(int grid) { return kFold * grid; }
 
 // Store this block's record (thread 0 holds v); returns true, in every
-// thread, in the last block to finish.
+// thread, in the last block to finish.  The ticket is a release-acquire
+// atomic at GPU scope: it orders each block's record store before its
+// ticket, and the last block's acquire -- extended to its other threads by
+// the barrier -- makes every record visible, with no separate fences.
 template <int N>
 __device__ inline bool publish_last(const double (&v)[N], double* part, unsigned int* counter, int* s_flag) {
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < N; ++q) part[(size_t)blockIdx.x * kMaxPartials + q] = v[q];
-    __threadfence();
-    *s_flag = atomicAdd(counter, 1u) == gridDim.x - 1;
+    unsigned int t;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(t) : "l"(counter) : "memory");
+    *s_flag = t == gridDim.x - 1;
   }
   __syncthreads();
-  if (*s_flag) __threadfence();
   return *s_flag != 0;
 }
 
@@ -351,6 +355,31 @@ __device__ inline void block_sum_records(const double* rec, int count, const dou
       for (int f = 0; f < N; ++f) out[f] = smem[f];
     }
   }
+}
+
+// Programmatic dependent launch of the kernels of a check period.  Each
+// starts with pdl_wait() (its predecessor has completed and its writes are
+// visible) and calls pdl_trigger() only once the rest of its grid is done:
+// at the end of a block for the primal kernels, in the last block only --
+// before its reduction and control -- for the dual kernels.  The successor's
+// blocks then become resident while that single block finishes, not while
+// the whole grid still runs (letting them in earlier, at kernel start, made
+// graph replay slower).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(kBlock, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);  // errors surface through cudaGetLastError
 }
 
 // ---------------------------------------------------------------------------

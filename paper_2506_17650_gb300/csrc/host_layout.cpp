@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <thread>
 
 #include "../../include/lpop.h"
 
@@ -33,7 +34,38 @@ int widen_factor(long long rows, long long target_threads) {
   return f;
 }
 
-// Stable permutation of rows by bin rank.
+// Run fn(begin, end) over [0, count) split into contiguous pieces, on up to 8
+// host threads when the range is large.
+template <class Fn>
+void parallel_ranges(long long count, Fn fn) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  int t = (int)std::min<unsigned>(hw == 0 ? 1u : hw, 8u);
+  if (count < (1 << 16)) t = 1;
+  if (t <= 1) {
+    fn(0LL, count);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int i = 0; i < t; ++i) {
+    const long long b = count * i / t, e = count * (i + 1) / t;
+    pool.emplace_back([=]() { fn(b, e); });
+  }
+  for (auto& th : pool) th.join();
+}
+
+// Run fn(t) for t in [0, T) on T host threads (T = 1: inline).
+template <class Fn>
+void parallel_ranges_n(int T, Fn fn) {
+  if (T <= 1) {
+    fn(0);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < T; ++t) pool.emplace_back([=]() { fn(t); });
+  for (auto& th : pool) th.join();
+}
+
+// Stable permutation of rows by bin rank, longest first within a bin.
 std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<int>& widths_sorted,
                                  std::vector<int>& lengths_sorted, long long target_threads) {
   const int rows = (int)len.size();
@@ -41,13 +73,24 @@ std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<
   std::vector<int> width(rows);
   for (int r = 0; r < rows; ++r) width[r] = width_for_length(len[r], widen);
   std::vector<int> perm(rows);
-  std::iota(perm.begin(), perm.end(), 0);
-  // by bin, then longest first within a bin (a warp's rows get similar lengths;
-  // the heaviest units come first)
-  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
-    const int ra = bin_rank(width[a]), rb = bin_rank(width[b]);
-    return ra != rb ? ra < rb : len[a] > len[b];
-  });
+  // a warp's rows get similar lengths and the heaviest units come first.
+  // Counting sort on (rank, length) for rows up to kCountMax entries; the few
+  // longer rows (all in the whole-block bin) are sorted directly and go first.
+  constexpr int kCountMax = 4096;
+  std::vector<int> longer;
+  std::vector<long long> start(7 * (kCountMax + 1) + 1, 0);
+  auto key = [&](int r) { return bin_rank(width[r]) * (kCountMax + 1) + (kCountMax - (int)len[r]); };
+  for (int r = 0; r < rows; ++r) {
+    if (len[r] > kCountMax) longer.push_back(r);
+    else start[key(r) + 1]++;
+  }
+  std::stable_sort(longer.begin(), longer.end(), [&](int a, int b) { return len[a] > len[b]; });
+  int pos = 0;
+  for (int r : longer) perm[pos++] = r;
+  start[0] = pos;
+  for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+  for (int r = 0; r < rows; ++r)
+    if (len[r] <= kCountMax) perm[start[key(r)]++] = r;
   widths_sorted.resize(rows);
   lengths_sorted.resize(rows);
   for (int r = 0; r < rows; ++r) {
@@ -97,7 +140,7 @@ BinTable make_bins(const std::vector<int>& widths_sorted, const std::vector<int>
     b.len = sliced ? lengths_sorted[r] : 0;
     b.base = sliced ? sell : 0;
     if (sliced) sell += (long long)(e - r + 31) / 32 * 32 * b.len;
-    const int per = rows_per_unit(b.width);
+    const int per = rows_per_unit(b);
     t.nunits += (e - r + per - 1) / per;
     r = e;
   }
@@ -168,27 +211,72 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
     }
   }
 
-  // sort each row by column and merge repeated entries (summed)
+  // sort each row by column and merge repeated entries (summed); row ranges
+  // on host threads, each into its own buffers, then concatenated
   std::vector<int64_t> rp(m + 1, 0);
   std::vector<int> ci;
   std::vector<double> cv;
-  ci.reserve(nnz);
-  cv.reserve(nnz);
-  std::vector<std::pair<int, double>> row;
-  for (int i = 0; i < m; ++i) {
-    row.clear();
-    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) row.emplace_back(col_idx[k], val[k]);
-    std::stable_sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
-    for (size_t t = 0; t < row.size();) {
-      const int c = row[t].first;
-      double s = row[t].second;
-      size_t e = t + 1;
-      while (e < row.size() && row[e].first == c) s += row[e++].second;
-      ci.push_back(c);
-      cv.push_back(s);
-      t = e;
+  {
+    struct Part {
+      long long r0 = 0, r1 = 0;
+      std::vector<int> ci;
+      std::vector<double> cv;
+      std::vector<int64_t> len;
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int T = nnz < (1 << 16) ? 1 : (int)std::min<unsigned>(hw == 0 ? 1u : hw, 8u);
+    std::vector<Part> parts(T);
+    for (int t = 0; t < T; ++t) {
+      parts[t].r0 = (long long)m * t / T;
+      parts[t].r1 = (long long)m * (t + 1) / T;
     }
-    rp[i + 1] = (int64_t)ci.size();
+    auto work = [&](Part& P) {
+      std::vector<std::pair<int, double>> row;
+      P.ci.reserve(row_ptr[P.r1] - row_ptr[P.r0]);
+      P.cv.reserve(row_ptr[P.r1] - row_ptr[P.r0]);
+      P.len.reserve(P.r1 - P.r0);
+      for (long long i = P.r0; i < P.r1; ++i) {
+        const size_t before = P.ci.size();
+        bool sorted = true;
+        for (int64_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) sorted = sorted && col_idx[k - 1] < col_idx[k];
+        if (sorted) {  // the common case: copy as is
+          P.ci.insert(P.ci.end(), col_idx + row_ptr[i], col_idx + row_ptr[i + 1]);
+          P.cv.insert(P.cv.end(), val + row_ptr[i], val + row_ptr[i + 1]);
+        } else {
+          row.clear();
+          for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) row.emplace_back(col_idx[k], val[k]);
+          std::stable_sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+          for (size_t t = 0; t < row.size();) {
+            const int c = row[t].first;
+            double sum = row[t].second;
+            size_t e = t + 1;
+            while (e < row.size() && row[e].first == c) sum += row[e++].second;
+            P.ci.push_back(c);
+            P.cv.push_back(sum);
+            t = e;
+          }
+        }
+        P.len.push_back((int64_t)(P.ci.size() - before));
+      }
+    };
+    if (T == 1) {
+      work(parts[0]);
+    } else {
+      std::vector<std::thread> pool;
+      for (int t = 0; t < T; ++t) pool.emplace_back([&, t]() { work(parts[t]); });
+      for (auto& th : pool) th.join();
+    }
+    long long total = 0;
+    for (const Part& P : parts) total += (long long)P.ci.size();
+    ci.resize(total);
+    cv.resize(total);
+    long long off = 0;
+    for (const Part& P : parts) {
+      std::copy(P.ci.begin(), P.ci.end(), ci.begin() + off);
+      std::copy(P.cv.begin(), P.cv.end(), cv.begin() + off);
+      for (long long i = P.r0; i < P.r1; ++i) rp[i + 1] = rp[i] + P.len[i - P.r0];
+      off += (long long)P.ci.size();
+    }
   }
   const long long nz = (long long)ci.size();
 
@@ -209,37 +297,75 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
 
   // permuted CSR of A, rows in bin order, column indices permuted and sorted
   out.A_rp.assign(m + 1, 0);
+  for (int ip = 0; ip < m; ++ip) out.A_rp[ip + 1] = out.A_rp[ip] + (int)rlen[out.prow[ip]];
   out.A_ci.resize(nz);
   out.A_v.resize(nz);
-  std::vector<std::pair<int, double>> tmp;
-  int64_t pos = 0;
-  for (int ip = 0; ip < m; ++ip) {
-    const int i = out.prow[ip];
-    tmp.clear();
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) tmp.emplace_back(icol[ci[k]], cv[k]);
-    std::sort(tmp.begin(), tmp.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
-    for (const auto& e : tmp) {
-      out.A_ci[pos] = e.first;
-      out.A_v[pos] = e.second;
-      ++pos;
+  parallel_ranges(m, [&](long long b, long long e) {
+    std::vector<std::pair<int, double>> tmp;
+    for (long long ip = b; ip < e; ++ip) {
+      const int i = out.prow[ip];
+      const int64_t src = rp[i], len = rp[i + 1] - rp[i];
+      const int dst = out.A_rp[ip];
+      bool sorted = true;
+      for (int64_t k = 0; k < len; ++k) {
+        out.A_ci[dst + k] = icol[ci[src + k]];
+        out.A_v[dst + k] = cv[src + k];
+        if (k > 0 && out.A_ci[dst + k - 1] > out.A_ci[dst + k]) sorted = false;
+      }
+      if (!sorted) {
+        tmp.clear();
+        for (int64_t k = 0; k < len; ++k) tmp.emplace_back(out.A_ci[dst + k], out.A_v[dst + k]);
+        std::sort(tmp.begin(), tmp.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+        for (int64_t k = 0; k < len; ++k) {
+          out.A_ci[dst + k] = tmp[k].first;
+          out.A_v[dst + k] = tmp[k].second;
+        }
+      }
     }
-    out.A_rp[ip + 1] = (int)pos;
-  }
+  });
 
-  // permuted CSR of A^T by counting sort (row indices come out sorted)
+  // permuted CSR of A^T by counting sort (row indices come out sorted): rows
+  // of A in T contiguous chunks, per-chunk column counts give every chunk its
+  // own start in each column, so the chunks fill in parallel
   out.At_rp.assign(n + 1, 0);
   for (long long k = 0; k < nz; ++k) out.At_rp[out.A_ci[k] + 1]++;
   for (int j = 0; j < n; ++j) out.At_rp[j + 1] += out.At_rp[j];
   out.At_ci.resize(nz);
   out.At_v.resize(nz);
-  std::vector<int> fillp(out.At_rp.begin(), out.At_rp.end() - 1);
-  for (int ip = 0; ip < m; ++ip) {
-    for (int k = out.A_rp[ip]; k < out.A_rp[ip + 1]; ++k) {
-      const int j = out.A_ci[k];
-      out.At_ci[fillp[j]] = ip;
-      out.At_v[fillp[j]] = out.A_v[k];
-      fillp[j]++;
-    }
+  {
+    const unsigned hw = std::thread::hardware_concurrency();
+    int T = nz < (1 << 17) ? 1 : (int)std::min<unsigned>(hw == 0 ? 1u : hw, 8u);
+    while (T > 1 && (long long)T * n > (32LL << 20)) --T;  // bound the count table
+    std::vector<int> fill((size_t)T * n);
+    parallel_ranges_n(T, [&](int t) {
+      int* f = fill.data() + (size_t)t * n;
+      std::fill(f, f + n, 0);
+      const long long r0 = (long long)m * t / T, r1 = (long long)m * (t + 1) / T;
+      for (long long k = out.A_rp[r0]; k < out.A_rp[r1]; ++k) f[out.A_ci[k]]++;
+    });
+    parallel_ranges(n, [&](long long b, long long e) {
+      for (long long j = b; j < e; ++j) {
+        int at = out.At_rp[j];
+        for (int t = 0; t < T; ++t) {
+          int& f = fill[(size_t)t * n + j];
+          const int c = f;
+          f = at;
+          at += c;
+        }
+      }
+    });
+    parallel_ranges_n(T, [&](int t) {
+      int* f = fill.data() + (size_t)t * n;
+      const long long r0 = (long long)m * t / T, r1 = (long long)m * (t + 1) / T;
+      for (long long ip = r0; ip < r1; ++ip) {
+        for (int k = out.A_rp[ip]; k < out.A_rp[ip + 1]; ++k) {
+          const int j = out.A_ci[k];
+          out.At_ci[f[j]] = (int)ip;
+          out.At_v[f[j]] = out.A_v[k];
+          f[j]++;
+        }
+      }
+    });
   }
   build_sliced(out.binsA, out.A_rp, out.A_ci, out.A_sell_ci, out.A_sell_pos);
   build_sliced(out.binsAt, out.At_rp, out.At_ci, out.At_sell_ci, out.At_sell_pos);
@@ -290,7 +416,7 @@ std::vector<int> segment_long_rows(BinTable& bt, const std::vector<int>& rp, int
   for (int b = 1; b < bt.nbins; ++b) {
     Bin x = bt.bin[b];
     x.unit_begin = unit;
-    const int per = rows_per_unit(x.width);
+    const int per = rows_per_unit(x);
     unit += (x.row_end - x.row_begin + per - 1) / per;
     out.bin[out.nbins++] = x;
   }

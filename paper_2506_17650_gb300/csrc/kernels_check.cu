@@ -24,6 +24,7 @@ namespace {
 template <bool AVG, class V>
 __global__ void __launch_bounds__(kBlock) check_primal_kernel(Dev d) {
   __shared__ double smem[kBlock * 10];
+  pdl_wait();
   constexpr int NV = AVG ? 2 : 1;
   const Vecs<V>& v = vecs<V>(d);
   const DevState* st = d.st;
@@ -45,11 +46,13 @@ __global__ void __launch_bounds__(kBlock) check_primal_kernel(Dev d) {
 #pragma unroll
     for (int q = 0; q < 10; ++q) rec[q] = op.acc[q];
   }
+  pdl_trigger();
 }
 
 template <bool AVG, class V>
 __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, int eval_only) {
   __shared__ double smem[kBlock * 8];
+  pdl_wait();
   __shared__ double fold[kFold * 10];
   const int nfold = fold_begin<10>(d.partials, partial_rows_at(d), fold);
   const Vecs<V>& v = vecs<V>(d);
@@ -91,6 +94,7 @@ __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, i
   }
   __shared__ int s_last;
   if (!publish_last<18>(rec, d.partials2, &st->counter, &s_last)) return;
+  pdl_trigger();
   double tot[18];
   // the segmented rows of A write their slots only when the average's product runs
   const int f0 = unfolded_first(d.gridA), np = partial_rows_at(d);
@@ -112,6 +116,8 @@ __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, i
 
 template <class V>
 __global__ void check_apply_kernel(Dev d) {
+  pdl_wait();
+  pdl_trigger();
   const DevState s = *d.st;
   apply_decision<V>(d, s, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
@@ -124,17 +130,17 @@ template <class V>
 void launch_check_t(const Dev& d, const Params& prm, int eval_only, cudaStream_t s) {
   const bool avg = prm.mode == kPdlp && eval_only != 1;
   if (avg) {
-    check_primal_kernel<true, V><<<d.gridAt, kBlock, 0, s>>>(d);
-    check_dual_kernel<true, V><<<d.gridA, kBlock, 0, s>>>(d, prm, eval_only);
+    launch_pdl(check_primal_kernel<true, V>, d.gridAt, s, d);
+    launch_pdl(check_dual_kernel<true, V>, d.gridA, s, d, prm, eval_only);
   } else {
-    check_primal_kernel<false, V><<<d.gridAt, kBlock, 0, s>>>(d);
-    check_dual_kernel<false, V><<<d.gridA, kBlock, 0, s>>>(d, prm, eval_only);
+    launch_pdl(check_primal_kernel<false, V>, d.gridAt, s, d);
+    launch_pdl(check_dual_kernel<false, V>, d.gridA, s, d, prm, eval_only);
   }
   const int rows = d.n > d.m ? d.n : d.m;
   int grid = (rows + kBlock - 1) / kBlock;
   if (grid > 4 * 152) grid = 4 * 152;
   if (grid < 1) grid = 1;
-  check_apply_kernel<V><<<grid, kBlock, 0, s>>>(d);
+  launch_pdl(check_apply_kernel<V>, grid, s, d);
 }
 
 void launch_check(const Dev& d, const Params& prm, int eval_only, bool fp32, cudaStream_t s) {

@@ -33,6 +33,7 @@ namespace {
 template <class V>
 __global__ void __launch_bounds__(kBlock, 3) primal_step_kernel(Dev d, Params prm) {
   __shared__ double smem[kBlock * 3];
+  pdl_wait();
   const Vecs<V>& v = vecs<V>(d);
   PrimalOp<V> op;
   op.sc = read_scalars<V>(d.st, true);
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(kBlock, 3) primal_step_kernel(Dev d, Params pr
     double* rec = d.partials + (size_t)blockIdx.x * kMaxPartials;
     rec[0] = a[0]; rec[1] = a[1]; rec[2] = a[2];
   }
+  pdl_trigger();
 }
 
 template <class V>
@@ -60,6 +62,7 @@ __global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm)
   __shared__ double fold[kFold * 3];
   __shared__ DevState s_st;  // the state does not change until the step control, at the very end
   __shared__ double s_f[2];
+  pdl_wait();
   // copied while the rows run: this block's share of the primal kernel's
   // records, and the state for the step control
   const int nfold = fold_begin<3>(d.partials, partial_rows_at(d), fold);
@@ -101,6 +104,7 @@ __global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm)
   }
   __shared__ int s_last;
   if (!publish_last<7>(rec, d.partials2, &d.st->counter, &s_last)) return;
+  pdl_trigger();  // the other blocks have exited: let the next kernel launch during the control
   // totals: this kernel's records (own sums, folded primal sums) and its
   // segmented rows' slots, then any primal records beyond the folded ones
   double tot[7];
@@ -167,13 +171,13 @@ int elementwise_grid(const Dev& d) {
 }  // namespace
 
 void launch_primal(const Dev& d, const Params& prm, bool fp32, cudaStream_t s) {
-  if (fp32) primal_step_kernel<float><<<d.gridAt, kBlock, 0, s>>>(d, prm);
-  else primal_step_kernel<double><<<d.gridAt, kBlock, 0, s>>>(d, prm);
+  if (fp32) launch_pdl(primal_step_kernel<float>, d.gridAt, s, d, prm);
+  else launch_pdl(primal_step_kernel<double>, d.gridAt, s, d, prm);
 }
 
 void launch_dual(const Dev& d, const Params& prm, bool fp32, cudaStream_t s) {
-  if (fp32) dual_step_kernel<float><<<d.gridA, kBlock, 0, s>>>(d, prm);
-  else dual_step_kernel<double><<<d.gridA, kBlock, 0, s>>>(d, prm);
+  if (fp32) launch_pdl(dual_step_kernel<float>, d.gridA, s, d, prm);
+  else launch_pdl(dual_step_kernel<double>, d.gridA, s, d, prm);
 }
 
 void launch_flush_update(const Dev& d, const Params& prm, bool fp32, cudaStream_t s) {

@@ -38,9 +38,11 @@ struct Bin {
   long long base;  // kSell: position of the bin's first entry in the sliced copy
 };
 
-// Rows per work unit of a bin width.
-inline int rows_per_unit(int width) {
-  return width == 0 || width == kSegmented ? 1 : (width == kSell ? kBlock : kBlock / width);
+// Rows per work unit of a bin.
+inline int rows_per_unit(const Bin& b) {
+  if (b.width == 0 || b.width == kSegmented) return 1;
+  if (b.width == kSell) return kBlock;
+  return kBlock / b.width;
 }
 
 struct BinTable {

@@ -200,6 +200,7 @@ __device__ inline void step_control_state(DevState& s, const Params& prm, double
     if (prm.mode == kPdlp) s.wsum += eta;
     s.cur ^= 1;
     s.k += 1;
+    if (prm.phi > 0) s.k_mod = s.k_mod + 1 == prm.phi ? 0 : s.k_mod + 1;
   }
   s.eta = eta_next;
   s.last_accept = accept ? 1 : 0;
