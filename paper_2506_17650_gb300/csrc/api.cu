@@ -5,6 +5,7 @@
 // device-resident iteration: one check period (check_every step attempts and
 // the KKT check) is captured once as a CUDA graph and replayed; the host only
 // reads one status word per period.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -20,7 +21,7 @@ using namespace lpop;
 
 namespace lpop {
 void launch_mul_into(double* out, const double* a, const double* f, int n, cudaStream_t s);
-void row_kernel_blocks_per_sm(int* primal, int* dual);
+void row_kernel_blocks_per_sm(int* primal, int* dual, int* primal32, int* dual32);
 }  // namespace lpop
 
 static thread_local std::string g_last_error;
@@ -351,9 +352,9 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
 
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  int per_sm_p = 1, per_sm_d = 1;
-  row_kernel_blocks_per_sm(&per_sm_p, &per_sm_d);
-  d.max_grid = sms * (per_sm_p > per_sm_d ? per_sm_p : per_sm_d);
+  int per_sm_p = 1, per_sm_d = 1, per_sm_p32 = 1, per_sm_d32 = 1;
+  row_kernel_blocks_per_sm(&per_sm_p, &per_sm_d, &per_sm_p32, &per_sm_d32);
+  d.max_grid = sms * std::max(std::max(per_sm_p, per_sm_d), std::max(per_sm_p32, per_sm_d32));
   d.binsA = lay.binsA;
   d.binsAt = lay.binsAt;
   // grids from the unit counts; rows longer than half a block's share of the
@@ -365,6 +366,8 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
       segment_long_rows(d.binsAt, lay.At_rp, segment_length(nz, grid_of(d.binsAt.nunits, cap_p)));
   d.gridA = grid_of(d.binsA.nunits, cap_d);
   d.gridAt = grid_of(d.binsAt.nunits, cap_p);
+  d.gridA32 = grid_of(d.binsA.nunits, sms * per_sm_d32);
+  d.gridAt32 = grid_of(d.binsAt.nunits, sms * per_sm_p32);
   for (int which = 0; which < 2; ++which) {
     BinTable& bt = which ? d.binsAt : d.binsA;
     const std::vector<int>& units = which ? segAt : segA;
@@ -391,7 +394,8 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
     CK(cudaMemcpyAsync(p->sell_pos[which], spos.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, p->stream));
   }
   CK(cudaStreamSynchronize(p->stream));
-  const int rows_a = partial_rows_a(d), rows_at = partial_rows_at(d);
+  const int rows_a = std::max(partial_rows_a<double>(d), partial_rows_a<float>(d));
+  const int rows_at = std::max(partial_rows_at<double>(d), partial_rows_at<float>(d));
   const int maxg = rows_a > rows_at ? rows_a : rows_at;
   TRY(dalloc(p, &d.partials, (size_t)maxg * kMaxPartials));
   TRY(dalloc(p, &d.partials2, (size_t)maxg * kMaxPartials));

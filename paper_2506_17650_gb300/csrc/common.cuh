@@ -150,19 +150,31 @@ struct Dev {
   const double* step_tab;  // [2 * kStepTab]: 1 - (t+1)^-0.3 and 1 + (t+1)^-0.6 for t < kStepTab
   DevState* st;
   BinTable binsA, binsAt;
-  int gridA, gridAt;  // blocks launched for the A / A^T row kernels
+  int gridA, gridAt;      // blocks launched for the A / A^T row kernels (FP64)
+  int gridA32, gridAt32;  // the same for the FP32 kernels (fewer registers, more resident blocks)
   int max_grid;
 };
 
-// Slots of the segmented rows within a partials array; records of a partials array.
+// Grids of the row kernels of precision V.
+template <class V>
+__host__ __device__ inline int grid_at(const Dev& d) { return sizeof(V) == 4 ? d.gridAt32 : d.gridAt; }
+template <class V>
+__host__ __device__ inline int grid_a(const Dev& d) { return sizeof(V) == 4 ? d.gridA32 : d.gridA; }
+
+// Slots of the segmented rows within a partials array (after the block
+// records of the precision-V kernels); records to sum.
+template <class V>
 __host__ __device__ inline double* row_slots_at(const Dev& d, double* part) {
-  return part + (size_t)d.gridAt * kMaxPartials;
+  return part + (size_t)grid_at<V>(d) * kMaxPartials;
 }
+template <class V>
 __host__ __device__ inline double* row_slots_a(const Dev& d, double* part) {
-  return part + (size_t)d.gridA * kMaxPartials;
+  return part + (size_t)grid_a<V>(d) * kMaxPartials;
 }
-__host__ __device__ inline int partial_rows_at(const Dev& d) { return d.gridAt + d.binsAt.seg_rows; }
-__host__ __device__ inline int partial_rows_a(const Dev& d) { return d.gridA + d.binsA.seg_rows; }
+template <class V>
+__host__ __device__ inline int partial_rows_at(const Dev& d) { return grid_at<V>(d) + d.binsAt.seg_rows; }
+template <class V>
+__host__ __device__ inline int partial_rows_a(const Dev& d) { return grid_a<V>(d) + d.binsA.seg_rows; }
 
 template <class V>
 __host__ __device__ inline const Vecs<V>& vecs(const Dev& d);

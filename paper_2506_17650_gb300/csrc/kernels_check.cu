@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kBlock) check_primal_kernel(Dev d) {
   Gather<NV, V> g;
   g.x[0] = v.y[cur];
   if (NV > 1) g.x[NV - 1] = v.ybar[cur];
-  for_each_row<NV, V, double>(d.binsAt, csr_at<V>(d), g, op, smem, row_slots_at(d, d.partials));
+  for_each_row<NV, V, double>(d.binsAt, csr_at<V>(d), g, op, smem, row_slots_at<V>(d, d.partials));
   block_sum_smem<10>(op.acc, smem);
   if (threadIdx.x == 0) {
     double* rec = d.partials + (size_t)blockIdx.x * kMaxPartials;
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, i
   __shared__ double smem[kBlock * 8];
   pdl_wait();
   __shared__ double fold[kFold * 10];
-  const int nfold = fold_begin<10>(d.partials, partial_rows_at(d), fold);
+  const int nfold = fold_begin<10>(d.partials, partial_rows_at<V>(d), fold);
   const Vecs<V>& v = vecs<V>(d);
   DevState* st = d.st;
   const int cur = st->cur;
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, i
   if (AVG) {
     Gather<1, V> g;
     g.x[0] = v.xbar[cur];
-    for_each_row<1, V, double>(d.binsA, csr_a<V>(d), g, op, smem, row_slots_a(d, d.partials2));
+    for_each_row<1, V, double>(d.binsA, csr_a<V>(d), g, op, smem, row_slots_a<V>(d, d.partials2));
   } else {
     // without an average candidate only the cached A x is needed: no sparse product
     const double s0[1] = {0.0};
@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, i
   pdl_trigger();
   double tot[18];
   // the segmented rows of A write their slots only when the average's product runs
-  const int f0 = unfolded_first(d.gridA), np = partial_rows_at(d);
-  block_sum_records<18, 10>(d.partials2, AVG ? partial_rows_a(d) : d.gridA, d.partials + (size_t)f0 * kMaxPartials,
+  const int f0 = unfolded_first(grid_a<V>(d)), np = partial_rows_at<V>(d);
+  block_sum_records<18, 10>(d.partials2, AVG ? partial_rows_a<V>(d) : grid_a<V>(d), d.partials + (size_t)f0 * kMaxPartials,
                             np > f0 ? np - f0 : 0, 8, tot, smem);
   double p1[10], p2[8];
 #pragma unroll
@@ -130,11 +130,11 @@ template <class V>
 void launch_check_t(const Dev& d, const Params& prm, int eval_only, cudaStream_t s) {
   const bool avg = prm.mode == kPdlp && eval_only != 1;
   if (avg) {
-    launch_pdl(check_primal_kernel<true, V>, d.gridAt, s, d);
-    launch_pdl(check_dual_kernel<true, V>, d.gridA, s, d, prm, eval_only);
+    launch_pdl(check_primal_kernel<true, V>, grid_at<V>(d), s, d);
+    launch_pdl(check_dual_kernel<true, V>, grid_a<V>(d), s, d, prm, eval_only);
   } else {
-    launch_pdl(check_primal_kernel<false, V>, d.gridAt, s, d);
-    launch_pdl(check_dual_kernel<false, V>, d.gridA, s, d, prm, eval_only);
+    launch_pdl(check_primal_kernel<false, V>, grid_at<V>(d), s, d);
+    launch_pdl(check_dual_kernel<false, V>, grid_a<V>(d), s, d, prm, eval_only);
   }
   const int rows = d.n > d.m ? d.n : d.m;
   int grid = (rows + kBlock - 1) / kBlock;

@@ -30,8 +30,14 @@ namespace lpop {
 
 namespace {
 
+// Resident blocks per SM the step kernels are compiled for: the FP64
+// instances need 80 registers a thread (3 blocks), the FP32 ones fit in 64
+// without spilling (4 blocks, a third more warps to hide latency).
 template <class V>
-__global__ void __launch_bounds__(kBlock, 3) primal_step_kernel(Dev d, Params prm) {
+constexpr int kStepBlocksPerSm = sizeof(V) == 4 ? 4 : 3;
+
+template <class V>
+__global__ void __launch_bounds__(kBlock, kStepBlocksPerSm<V>) primal_step_kernel(Dev d, Params prm) {
   __shared__ double smem[kBlock * 3];
   pdl_wait();
   const Vecs<V>& v = vecs<V>(d);
@@ -46,7 +52,7 @@ __global__ void __launch_bounds__(kBlock, 3) primal_step_kernel(Dev d, Params pr
   op.acc[0] = op.acc[1] = op.acc[2] = V(0);
   Gather<1, V> g;
   g.x[0] = v.y[cur];
-  for_each_row<1, V, V>(d.binsAt, csr_at<V>(d), g, op, smem, row_slots_at(d, d.partials));
+  for_each_row<1, V, V>(d.binsAt, csr_at<V>(d), g, op, smem, row_slots_at<V>(d, d.partials));
   double a[3] = {(double)op.acc[0], (double)op.acc[1], (double)op.acc[2]};
   block_sum_smem<3>(a, smem);
   if (threadIdx.x == 0) {
@@ -57,7 +63,7 @@ __global__ void __launch_bounds__(kBlock, 3) primal_step_kernel(Dev d, Params pr
 }
 
 template <class V>
-__global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm) {
+__global__ void __launch_bounds__(kBlock, kStepBlocksPerSm<V>) dual_step_kernel(Dev d, Params prm) {
   __shared__ double smem[kBlock * 7];
   __shared__ double fold[kFold * 3];
   __shared__ DevState s_st;  // the state does not change until the step control, at the very end
@@ -65,7 +71,7 @@ __global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm)
   pdl_wait();
   // copied while the rows run: this block's share of the primal kernel's
   // records, and the state for the step control
-  const int nfold = fold_begin<3>(d.partials, partial_rows_at(d), fold);
+  const int nfold = fold_begin<3>(d.partials, partial_rows_at<V>(d), fold);
   {
     static_assert(sizeof(DevState) % 8 == 0, "state copied in 8-byte words");
     const double* src = reinterpret_cast<const double*>(d.st);
@@ -84,7 +90,7 @@ __global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm)
   op.acc[0] = op.acc[1] = op.acc[2] = op.acc[3] = V(0);
   Gather<1, V> g;
   g.x[0] = v.x[nxt];  // x+ written by the primal kernel
-  for_each_row<1, V, V>(d.binsA, csr_a<V>(d), g, op, smem, row_slots_a(d, d.partials2));
+  for_each_row<1, V, V>(d.binsA, csr_a<V>(d), g, op, smem, row_slots_a<V>(d, d.partials2));
   double a[4] = {(double)op.acc[0], (double)op.acc[1], (double)op.acc[2], (double)op.acc[3]};
   block_sum_smem<4>(a, smem);
   cp_async_wait_all();
@@ -108,8 +114,8 @@ __global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm)
   // totals: this kernel's records (own sums, folded primal sums) and its
   // segmented rows' slots, then any primal records beyond the folded ones
   double tot[7];
-  const int f0 = unfolded_first(d.gridA), np = partial_rows_at(d);
-  block_sum_records<7, 3>(d.partials2, partial_rows_a(d), d.partials + (size_t)f0 * kMaxPartials,
+  const int f0 = unfolded_first(grid_a<V>(d)), np = partial_rows_at<V>(d);
+  block_sum_records<7, 3>(d.partials2, partial_rows_a<V>(d), d.partials + (size_t)f0 * kMaxPartials,
                           np > f0 ? np - f0 : 0, 4, tot, smem);
   if (threadIdx.x == 0) {
     const double t1[3] = {tot[4], tot[5], tot[6]};
@@ -122,9 +128,13 @@ __global__ void __launch_bounds__(kBlock, 3) dual_step_kernel(Dev d, Params prm)
     } else {
       step_factors(d.step_tab, tnext, &f1, &f2);
     }
-    DevState s = s_st;  // register copy, written back once
-    step_control_state(s, prm, f1, f2, t1, t2);
-    *d.st = s;
+    step_control_state(s_st, prm, f1, f2, t1, t2);  // on the shared copy: no register-held state
+  }
+  __syncthreads();
+  {  // written back by the block, word by word
+    const double* src = reinterpret_cast<const double*>(&s_st);
+    double* dst = reinterpret_cast<double*>(d.st);
+    for (int t = threadIdx.x; t < (int)(sizeof(DevState) / 8); t += blockDim.x) dst[t] = src[t];
   }
 }
 
@@ -171,12 +181,12 @@ int elementwise_grid(const Dev& d) {
 }  // namespace
 
 void launch_primal(const Dev& d, const Params& prm, bool fp32, cudaStream_t s) {
-  if (fp32) launch_pdl(primal_step_kernel<float>, d.gridAt, s, d, prm);
+  if (fp32) launch_pdl(primal_step_kernel<float>, d.gridAt32, s, d, prm);
   else launch_pdl(primal_step_kernel<double>, d.gridAt, s, d, prm);
 }
 
 void launch_dual(const Dev& d, const Params& prm, bool fp32, cudaStream_t s) {
-  if (fp32) launch_pdl(dual_step_kernel<float>, d.gridA, s, d, prm);
+  if (fp32) launch_pdl(dual_step_kernel<float>, d.gridA32, s, d, prm);
   else launch_pdl(dual_step_kernel<double>, d.gridA, s, d, prm);
 }
 
@@ -191,16 +201,18 @@ void launch_inverse_preconditioners(const Dev& d, bool fp32, cudaStream_t s) {
   else inverse_kernel<double><<<elementwise_grid(d), kBlock, 0, s>>>(d);
 }
 
-// Resident blocks per SM of the two step kernels (they size the grids; the
-// FP64 instances use more registers, so their occupancy bounds both).
-void row_kernel_blocks_per_sm(int* primal, int* dual) {
-  int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, primal_step_kernel<double>, kBlock, 0) != cudaSuccess || a < 1)
-    a = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, dual_step_kernel<double>, kBlock, 0) != cudaSuccess || b < 1)
-    b = 1;
-  *primal = a;
-  *dual = b;
+// Resident blocks per SM of the two step kernels, FP64 (primal, dual) and
+// FP32 (primal32, dual32); they size the grids.
+void row_kernel_blocks_per_sm(int* primal, int* dual, int* primal32, int* dual32) {
+  auto occ = [](auto kernel) {
+    int a = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, kernel, kBlock, 0) != cudaSuccess || a < 1) a = 1;
+    return a;
+  };
+  *primal = occ(primal_step_kernel<double>);
+  *dual = occ(dual_step_kernel<double>);
+  *primal32 = occ(primal_step_kernel<float>);
+  *dual32 = occ(dual_step_kernel<float>);
 }
 
 }  // namespace lpop
