@@ -614,7 +614,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="transport", choices=["transport", "powerlaw", "batch", "serve"])
     ap.add_argument("--batch-count", type=int, default=512)
-    ap.add_argument("--batch-handoff", type=int, default=2048,
+    ap.add_argument("--batch-handoff", type=int, default=1024,
                     help="attempts after which a batch member finishes on the single-problem kernels")
     ap.add_argument("--serve-count", type=int, default=24)
     ap.add_argument("--serve-max-nnz", type=float, default=1e7)
