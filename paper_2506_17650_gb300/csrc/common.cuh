@@ -331,15 +331,15 @@ __device__ inline void block_sum_records(const double* rec, int count, const dou
   const int q = t % N, sl = t / N;
   double acc = 0.0;
   if (sl < S) {
-    for (int r0 = sl; r0 < count; r0 += 4 * S) {  // up to 4 independent loads, then the adds
-      double v[4];
+    for (int r0 = sl; r0 < count; r0 += 8 * S) {  // up to 8 independent loads (one L2 round trip), then the adds
+      double v[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int r = r0 + u * S;
         v[u] = r < count ? __ldcg(rec + (size_t)r * kMaxPartials + q) : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc += v[u];
+      for (int u = 0; u < 8; ++u) acc += v[u];
     }
     if (q >= q2 && q < q2 + N2) {
       for (int r = sl; r < count2; r += S) acc += __ldcg(rec2 + (size_t)r * kMaxPartials + (q - q2));
