@@ -289,8 +289,9 @@ int lp_batch_round(lp_batch* b, double rel_kkt_tol, int32_t attempts, int64_t it
  * be NULL) receives how many members reached the tolerance.  With a handoff
  * (lp_batch_set_handoff), a member still open at a round boundary after at
  * least that many attempts leaves the batch and finishes with lp_solve (its
- * own full-grid kernels, on its own stream, from a host thread of this call)
- * while the batch goes on with the rest; the call returns when all are done.
+ * own full-grid kernels, on its own stream, from a pool of at most 16 host
+ * threads of this call) while the batch goes on with the rest; the call
+ * returns when all are done.
  * The rule depends only on the member's own attempts, so a member's result
  * does not depend on the rest of the batch. */
 int lp_batch_solve(lp_batch* b, double rel_kkt_tol, int64_t iter_limit, int32_t round_attempts, int32_t* n_optimal);

@@ -16,6 +16,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -674,8 +677,30 @@ int lp_batch_solve(lp_batch* b, double rel_kkt_tol, int64_t iter_limit, int32_t 
   if (round_attempts < 1) return berr(b, LP_ERR_INVALID_ARG, "round_attempts must be >= 1");
   const int count = (int)b->probs.size();
   b->handed.assign(count, 0);
-  std::vector<std::thread> workers;
   std::vector<int> worker_rc(count, LP_OK);
+  // handed-off members wait in a queue for a bounded pool of host threads
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<int> queue;
+  bool closed = false;
+  std::vector<std::thread> workers;
+  const unsigned hw = std::thread::hardware_concurrency();
+  const size_t max_workers = std::min<size_t>(16, hw == 0 ? 4 : hw);
+  const int dev = b->device;
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      int i;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return closed || !queue.empty(); });
+        if (queue.empty()) return;
+        i = queue.front();
+        queue.pop_front();
+      }
+      worker_rc[i] = lp_solve(b->probs[i], rel_kkt_tol, iter_limit, nullptr);
+    }
+  };
   int rc = LP_OK;
   int active = 1;
   long long guard = 0;
@@ -690,17 +715,21 @@ int lp_batch_solve(lp_batch* b, double rel_kkt_tol, int64_t iter_limit, int32_t 
         if (b->handed[i] || st.status != 0 || st.attempts >= iter_limit || st.attempts < b->handoff) continue;
         b->handed[i] = 1;
         --active;
-        lp_problem* p = b->probs[i];
-        int* out = &worker_rc[i];
-        const int dev = b->device;
-        workers.emplace_back([p, out, dev, rel_kkt_tol, iter_limit]() {
-          cudaSetDevice(dev);
-          *out = lp_solve(p, rel_kkt_tol, iter_limit, nullptr);
-        });
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          queue.push_back(i);
+        }
+        cv.notify_one();
+        if (workers.size() < max_workers) workers.emplace_back(worker);
       }
     }
     if (++guard > 100000000) break;
   }
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    closed = true;
+  }
+  cv.notify_all();
   for (std::thread& t : workers) t.join();
   b->handed.clear();
   if (rc != LP_OK) return rc;
