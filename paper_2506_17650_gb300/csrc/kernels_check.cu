@@ -21,8 +21,14 @@ namespace lpop {
 
 namespace {
 
+// The FP64 check kernels are compiled for 3 resident blocks per SM, so that
+// their grid (the FP64 step kernels' grid) runs in one wave; the FP32 ones
+// keep their registers (their grid is sized for 4 blocks per SM anyway).
+template <class V>
+constexpr int kCheckBlocksPerSm = sizeof(V) == 8 ? 3 : 1;
+
 template <bool AVG, class V>
-__global__ void __launch_bounds__(kBlock) check_primal_kernel(Dev d) {
+__global__ void __launch_bounds__(kBlock, kCheckBlocksPerSm<V>) check_primal_kernel(Dev d) {
   __shared__ double smem[kBlock * 10];
   pdl_wait();
   constexpr int NV = AVG ? 2 : 1;
@@ -50,7 +56,7 @@ __global__ void __launch_bounds__(kBlock) check_primal_kernel(Dev d) {
 }
 
 template <bool AVG, class V>
-__global__ void __launch_bounds__(kBlock) check_dual_kernel(Dev d, Params prm, int eval_only) {
+__global__ void __launch_bounds__(kBlock, kCheckBlocksPerSm<V>) check_dual_kernel(Dev d, Params prm, int eval_only) {
   __shared__ double smem[kBlock * 8];
   pdl_wait();
   __shared__ double fold[kFold * 10];
