@@ -66,7 +66,6 @@ struct lp_problem {
   // preprocessed values are final
   long long sell_n[2] = {0, 0};
   int* sell_ci[2] = {nullptr, nullptr};
-  int* sell_pos[2] = {nullptr, nullptr};
   double* sell_v[2] = {nullptr, nullptr};
   float* sell_v32[2] = {nullptr, nullptr};
 };
@@ -295,7 +294,8 @@ int preprocess(lp_problem* p) {
   for (int which = 0; which < 2; ++which) {
     if (p->sell_n[which] == 0) continue;
     BinTable& bt = which ? d.binsAt : d.binsA;
-    launch_gather_values(p->sell_pos[which], which ? d.At_v : d.A_v, p->sell_v[which], p->sell_n[which], s);
+    launch_fill_sliced(bt, which ? d.At_rp : d.A_rp, which ? d.At_ci : d.A_ci, which ? d.At_v : d.A_v,
+                       p->sell_ci[which], p->sell_v[which], p->sell_n[which], s);
     if (p->mixed) launch_narrow(p->sell_v[which], p->sell_v32[which], p->sell_n[which], s);
     bt.sell_ci = p->sell_ci[which];
     bt.sell_v = p->sell_v[which];
@@ -380,18 +380,13 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
     CK(cudaMemsetAsync(bt.ticket, 0, sizeof(unsigned int) * bt.seg_rows, p->stream));
     bt.seg_unit = su;
   }
-  for (int which = 0; which < 2; ++which) {
-    const std::vector<int>& sci = which ? lay.At_sell_ci : lay.A_sell_ci;
-    const std::vector<int>& spos = which ? lay.At_sell_pos : lay.A_sell_pos;
-    const long long ns = (long long)sci.size();
+  for (int which = 0; which < 2; ++which) {  // sliced copies: filled on the device once the values are final
+    const long long ns = sliced_entries(which ? d.binsAt : d.binsA);
     p->sell_n[which] = ns;
     if (ns == 0) continue;
     TRY(dalloc(p, &p->sell_ci[which], (size_t)ns));
-    TRY(dalloc(p, &p->sell_pos[which], (size_t)ns));
     TRY(dalloc(p, &p->sell_v[which], (size_t)ns));
     if (p->mixed) TRY(dalloc(p, &p->sell_v32[which], (size_t)ns));
-    CK(cudaMemcpyAsync(p->sell_ci[which], sci.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, p->stream));
-    CK(cudaMemcpyAsync(p->sell_pos[which], spos.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, p->stream));
   }
   CK(cudaStreamSynchronize(p->stream));
   const int rows_a = std::max(partial_rows_a<double>(d), partial_rows_a<float>(d));
@@ -1026,7 +1021,7 @@ int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, in
   t += 2 * r(8LL * kMaxPartials * (4096 + S));  // per-block records (upper bound of the grid) and row slots
   // sliced copies of the rows of up to 16 entries (at most nnz entries plus the padding of 17 bins' last slices)
   const long long SE = nnz + 17LL * 31 * 16;
-  t += 2 * (2 * r(4LL * SE) + r(8LL * SE) + (o.precision == LP_PREC_MIXED ? r(4LL * SE) : 0));
+  t += 2 * (r(4LL * SE) + r(8LL * SE) + (o.precision == LP_PREC_MIXED ? r(4LL * SE) : 0));
   *bytes = t;
   return LP_OK;
 }

@@ -409,8 +409,10 @@ void launch_flush_update(const Dev& d, const Params& prm, bool fp32, cudaStream_
 void launch_inverse_preconditioners(const Dev& d, bool fp32, cudaStream_t s);
 // mixed precision: FP32 copies of the problem data and the initial FP32 state
 void launch_make_fp32(const Dev& d, cudaStream_t s);
-// out[i] = pos[i] >= 0 ? v[pos[i]] : 0 (i < n)
-void launch_gather_values(const int* pos, const double* v, double* out, long long n, cudaStream_t s);
+// the sliced copy (column indices and values, `total` entries) of the kSell
+// bins of bt from the permuted CSR arrays rp, ci, v
+void launch_fill_sliced(const BinTable& bt, const int* rp, const int* ci, const double* v, int* sell_ci,
+                        double* sell_v, long long total, cudaStream_t s);
 // out[i] = (float)in[i]
 void launch_narrow(const double* in, float* out, long long n, cudaStream_t s);
 // FP32 iterate -> FP64 iterate (refinement phase); FP64 -> FP32 (state import)

@@ -2,6 +2,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -35,12 +36,13 @@ int widen_factor(long long rows, long long target_threads) {
 }
 
 // Run fn(begin, end) over [0, count) split into contiguous pieces, on up to 8
-// host threads when the range is large.
+// host threads when the work (count by default; e.g. the entries of the
+// rows when a range is rows) is large.
 template <class Fn>
-void parallel_ranges(long long count, Fn fn) {
+void parallel_ranges(long long count, Fn fn, long long work = -1) {
   const unsigned hw = std::thread::hardware_concurrency();
   int t = (int)std::min<unsigned>(hw == 0 ? 1u : hw, 8u);
-  if (count < (1 << 16)) t = 1;
+  if ((work < 0 ? count : work) < (1 << 16)) t = 1;
   if (t <= 1) {
     fn(0LL, count);
     return;
@@ -156,26 +158,6 @@ long long sliced_entries(const BinTable& bt) {
   return total;
 }
 
-void build_sliced(const BinTable& bt, const std::vector<int>& rp, const std::vector<int>& ci,
-                  std::vector<int>& sell_ci, std::vector<int>& sell_pos) {
-  const long long total = sliced_entries(bt);
-  sell_ci.assign((size_t)total, 0);
-  sell_pos.assign((size_t)total, -1);
-  for (int b = 0; b < bt.nbins; ++b) {
-    const Bin& x = bt.bin[b];
-    if (x.width != kSell) continue;
-    for (int i = 0; i < x.row_end - x.row_begin; ++i) {
-      const int row = x.row_begin + i;
-      const long long p0 = x.base + (long long)(i / 32) * 32 * x.len + (i % 32);
-      for (int k = 0; k < x.len; ++k) {
-        const long long p = p0 + 32LL * k;
-        sell_ci[(size_t)p] = ci[(size_t)rp[row] + k];
-        sell_pos[(size_t)p] = rp[row] + k;
-      }
-    }
-  }
-}
-
 int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                  const double* val, HostLayout& out, std::string& err, long long target_threads) {
   if (m < 0 || n < 1 || nnz < 0) {
@@ -200,23 +182,49 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
       return LP_ERR_INVALID_INPUT;
     }
   }
-  for (int64_t k = 0; k < nnz; ++k) {
-    if (col_idx[k] < 0 || col_idx[k] >= n) {
-      err = "col_idx[" + std::to_string(k) + "] out of range";
-      return LP_ERR_INVALID_INPUT;
-    }
-    if (!std::isfinite(val[k])) {
-      err = "val[" + std::to_string(k) + "] is not finite";
+  // entries (on host threads, by ranges of rows): the first one with a column
+  // out of range or a value that is not finite, and whether every row is in
+  // strictly increasing column order
+  bool canonical = true;
+  {
+    std::mutex mu;
+    int64_t bad = nnz;
+    auto scan = [&](long long r0, long long r1) {
+      int64_t first_bad = nnz;
+      bool inc = true;
+      for (long long i = r0; i < r1 && first_bad == nnz; ++i) {
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+          if (col_idx[k] < 0 || col_idx[k] >= n || !std::isfinite(val[k])) {
+            first_bad = k;
+            break;
+          }
+          inc = inc && (k == row_ptr[i] || col_idx[k - 1] < col_idx[k]);
+        }
+      }
+      std::lock_guard<std::mutex> lock(mu);
+      bad = std::min(bad, first_bad);
+      canonical = canonical && inc;
+    };
+    parallel_ranges(m, scan, nnz);
+    if (bad < nnz) {
+      err = col_idx[bad] < 0 || col_idx[bad] >= n ? "col_idx[" + std::to_string(bad) + "] out of range"
+                                                  : "val[" + std::to_string(bad) + "] is not finite";
       return LP_ERR_INVALID_INPUT;
     }
   }
 
-  // sort each row by column and merge repeated entries (summed); row ranges
-  // on host threads, each into its own buffers, then concatenated
-  std::vector<int64_t> rp(m + 1, 0);
-  std::vector<int> ci;
-  std::vector<double> cv;
-  {
+  // rows in strictly increasing column order (the common case) are used in
+  // place; otherwise each row is sorted by column and repeated entries are
+  // merged (summed), row ranges on host threads, each into its own buffers,
+  // then concatenated
+  std::vector<int64_t> rp_m;
+  std::vector<int> ci_m;
+  std::vector<double> cv_m;
+  if (!canonical) {
+    std::vector<int64_t>& rp = rp_m;
+    std::vector<int>& ci = ci_m;
+    std::vector<double>& cv = cv_m;
+    rp.assign(m + 1, 0);
     struct Part {
       long long r0 = 0, r1 = 0;
       std::vector<int> ci;
@@ -278,20 +286,31 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
       off += (long long)P.ci.size();
     }
   }
-  const long long nz = (long long)ci.size();
+  const int64_t* rp = canonical ? row_ptr : rp_m.data();
+  const int32_t* ci = canonical ? col_idx : ci_m.data();
+  const double* cv = canonical ? val : cv_m.data();
+  const long long nz = canonical ? (long long)nnz : (long long)ci_m.size();
 
+  // row and column orders (independent: the columns on a second thread)
   std::vector<long long> rlen(m), clen(n, 0);
-  for (int i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
-  for (long long k = 0; k < nz; ++k) clen[ci[k]]++;
-
   std::vector<int> wA, wAt, lA, lAt;
   out.m = m;
   out.n = n;
   out.nnz = nz;
-  out.prow = bin_permutation(rlen, wA, lA, target_threads);
-  out.pcol = bin_permutation(clen, wAt, lAt, target_threads);
-  out.binsA = make_bins(wA, lA);
-  out.binsAt = make_bins(wAt, lAt);
+  {
+    auto columns = [&]() {
+      for (long long k = 0; k < nz; ++k) clen[ci[k]]++;
+      out.pcol = bin_permutation(clen, wAt, lAt, target_threads);
+      out.binsAt = make_bins(wAt, lAt);
+    };
+    std::thread th;
+    if (nz >= (1 << 16)) th = std::thread(columns);
+    for (int i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
+    out.prow = bin_permutation(rlen, wA, lA, target_threads);
+    out.binsA = make_bins(wA, lA);
+    if (th.joinable()) th.join();
+    else columns();
+  }
   std::vector<int> icol(n);
   for (int j = 0; j < n; ++j) icol[out.pcol[j]] = j;
 
@@ -300,7 +319,7 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
   for (int ip = 0; ip < m; ++ip) out.A_rp[ip + 1] = out.A_rp[ip] + (int)rlen[out.prow[ip]];
   out.A_ci.resize(nz);
   out.A_v.resize(nz);
-  parallel_ranges(m, [&](long long b, long long e) {
+  auto permute_rows = [&](long long b, long long e) {
     std::vector<std::pair<int, double>> tmp;
     for (long long ip = b; ip < e; ++ip) {
       const int i = out.prow[ip];
@@ -322,14 +341,14 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
         }
       }
     }
-  });
+  };
+  parallel_ranges(m, permute_rows, nz);  // ranges of rows, sized by their entries
 
   // permuted CSR of A^T by counting sort (row indices come out sorted): rows
   // of A in T contiguous chunks, per-chunk column counts give every chunk its
   // own start in each column, so the chunks fill in parallel
   out.At_rp.assign(n + 1, 0);
-  for (long long k = 0; k < nz; ++k) out.At_rp[out.A_ci[k] + 1]++;
-  for (int j = 0; j < n; ++j) out.At_rp[j + 1] += out.At_rp[j];
+  for (int j = 0; j < n; ++j) out.At_rp[j + 1] = out.At_rp[j] + (int)clen[out.pcol[j]];
   out.At_ci.resize(nz);
   out.At_v.resize(nz);
   {
@@ -367,8 +386,6 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
       }
     });
   }
-  build_sliced(out.binsA, out.A_rp, out.A_ci, out.A_sell_ci, out.A_sell_pos);
-  build_sliced(out.binsAt, out.At_rp, out.At_ci, out.At_sell_ci, out.At_sell_pos);
   return LP_OK;
 }
 

@@ -19,9 +19,6 @@ struct HostLayout {
   std::vector<int> A_rp, A_ci, At_rp, At_ci;
   std::vector<double> A_v, At_v;
   BinTable binsA{}, binsAt{};
-  // sliced copies of the kSell bins: column index and CSR position of each
-  // entry (-1 for the padding of a bin's last slice)
-  std::vector<int> A_sell_ci, A_sell_pos, At_sell_ci, At_sell_pos;
 };
 
 // Lanes per row for a row of length len: 1, 2, 4, ..., 32, or 0 (a block per
@@ -41,12 +38,9 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
 // length each (no kSell bins when lengths_sorted is empty).
 BinTable make_bins(const std::vector<int>& widths_sorted, const std::vector<int>& lengths_sorted);
 
-// Entries of the sliced copy of a table's kSell bins (padding included).
+// Entries of the sliced copy of a table's kSell bins (padding included); the
+// copy itself is filled on the device.
 long long sliced_entries(const BinTable& bt);
-
-// The sliced copy of a permuted CSR matrix's kSell bins.
-void build_sliced(const BinTable& bt, const std::vector<int>& rp, const std::vector<int>& ci,
-                  std::vector<int>& sell_ci, std::vector<int>& sell_pos);
 
 // Segment length for a matrix of nnz entries processed by `grid` blocks.
 int segment_length(long long nnz, int grid);

@@ -232,10 +232,32 @@ __global__ void __launch_bounds__(kBlock) recompute_ax_kernel(Dev d) {
   for_each_row<1, double, double>(d.binsA, d.A, g, op, smem);
 }
 
-__global__ void gather_values_kernel(const int* pos, const double* v, double* out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int k = pos[i];
-    out[i] = k >= 0 ? v[k] : 0.0;
+// Entry p of the sliced copy: in the kSell bin with the largest base <= p,
+// off = p - base = slice * 32 len + 32 k + t is entry k of row slice * 32 + t
+// of the bin; rows past the bin's end (padding of its last slice) get
+// column 0 and value 0.
+__global__ void fill_sliced_kernel(BinTable bt, const int* rp, const int* ci, const double* v, int* sell_ci,
+                                   double* sell_v, long long total) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total; p += (long long)gridDim.x * blockDim.x) {
+    int b = -1;
+    for (int q = 0; q < bt.nbins; ++q)
+      if (bt.bin[q].width == kSell && bt.bin[q].base <= p) b = q;
+    int c = 0;
+    double x = 0.0;
+    if (b >= 0) {
+      const Bin& B = bt.bin[b];
+      const long long off = p - B.base, per = 32LL * B.len;
+      const long long slice = off / per;
+      const int rem = (int)(off - slice * per);
+      const long long row = B.row_begin + slice * 32 + (rem & 31);
+      if (row < B.row_end) {
+        const long long src = (long long)rp[row] + (rem >> 5);
+        c = ci[src];
+        x = v[src];
+      }
+    }
+    sell_ci[p] = c;
+    sell_v[p] = x;
   }
 }
 
@@ -322,8 +344,9 @@ void launch_init_vectors(const Dev& d, cudaStream_t s) {
 
 namespace lpop {
 
-void launch_gather_values(const int* pos, const double* v, double* out, long long n, cudaStream_t s) {
-  if (n > 0) gather_values_kernel<<<grid_for(n), kBlock, 0, s>>>(pos, v, out, n);
+void launch_fill_sliced(const BinTable& bt, const int* rp, const int* ci, const double* v, int* sell_ci,
+                        double* sell_v, long long total, cudaStream_t s) {
+  if (total > 0) fill_sliced_kernel<<<grid_for(total), kBlock, 0, s>>>(bt, rp, ci, v, sell_ci, sell_v, total);
 }
 
 void launch_narrow(const double* in, float* out, long long n, cudaStream_t s) {

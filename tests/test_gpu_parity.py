@@ -320,6 +320,40 @@ def test_runs_are_deterministic_and_reset_restores_the_start():
         assert np.array_equal(start[key], again[key])
 
 
+def test_unsorted_rows_and_repeated_entries_give_the_same_solve():
+    """lp_create sorts each row by column and sums repeated entries: an LP whose
+    rows are shuffled and whose entries are partly split into two exact halves
+    is the same LP, so its solve is bitwise the same."""
+    lp = lpgen.row_length_mix(2)
+    rng = np.random.default_rng(5)
+    rows_ci, rows_v, rp = [], [], [0]
+    for i in range(lp.m):
+        a, b = lp.row_ptr[i], lp.row_ptr[i + 1]
+        ci, v = list(lp.col_idx[a:b]), list(lp.val[a:b])
+        for k in rng.choice(len(ci), size=min(len(ci), 2), replace=False) if len(ci) else []:
+            v[k] = v[k] / 2  # exact: the two halves add back to the value
+            ci.append(ci[k])
+            v.append(v[k])
+        perm = rng.permutation(len(ci))
+        rows_ci += [ci[t] for t in perm]
+        rows_v += [v[t] for t in perm]
+        rp.append(len(rows_ci))
+    messy = copy.copy(lp)
+    messy.row_ptr = np.asarray(rp, dtype=np.int64)
+    messy.col_idx = np.asarray(rows_ci, dtype=np.int32)
+    messy.val = np.asarray(rows_v, dtype=np.float64)
+    assert messy.nnz > lp.nnz
+    o = oracle.Options(alpha=1e-3, phi=5)
+    out = []
+    for q in (lp, messy):
+        with lpop.Problem(q, **gpu_options(o)) as p:
+            p.solve(0.0, 300)
+            out.append(p.iterate())
+    for key in ("x", "y", "T", "Sigma"):
+        assert np.array_equal(out[0][key], out[1][key]), key
+    assert out[0]["eta"] == out[1]["eta"] and out[0]["omega"] == out[1]["omega"]
+
+
 def test_alpha_zero_keeps_identity_preconditioners():
     lp = lpgen.mixed_small(4)
     o = oracle.Options(alpha=0.0, phi=1)
