@@ -377,6 +377,7 @@ def gpu_arm(args):
             "config": dict(base_config(kind), **({"step": "640 step attempts from the initial point",
                                                   "scale": args.scale} if large else {})),
             "time_to_tol_ms": None if large else statistics.median(step_ms),
+            "step_ms": [round(t, 3) for t in step_ms],
             "iterations_per_solve": last["iterations"],
             "status": ("iteration limit (fixed-length steps)" if large else
                        "optimal" if all(s_ == lpop.LP_OPTIMAL for s_ in statuses) else str(statuses)),

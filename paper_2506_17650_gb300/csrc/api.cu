@@ -60,11 +60,16 @@ struct lp_problem {
   long long kt_n[2] = {0, 0};
   int* h_status = nullptr;  // pinned
   double* h_scratch = nullptr;  // pinned, 8 doubles
+  // device memory: one allocation of the lp_memory_bytes bound, handed out
+  // by dalloc in 256-byte steps; anything beyond it gets its own cudaMalloc
+  char* arena = nullptr;
+  size_t arena_size = 0, arena_used = 0;
   std::vector<void*> allocs;
   // sliced copies of the kSell bins of A (0) and A^T (1): entries, column
-  // indices, CSR positions (-1 = padding) and the values, filled once the
-  // preprocessed values are final
+  // indices and values, filled on the device once the preprocessed values
+  // are final
   long long sell_n[2] = {0, 0};
+  int split[2] = {0, 0};  // first row of A / A^T with at most 32 entries (rows are sorted longest first)
   int* sell_ci[2] = {nullptr, nullptr};
   double* sell_v[2] = {nullptr, nullptr};
   float* sell_v32[2] = {nullptr, nullptr};
@@ -124,6 +129,12 @@ template <class T>
 int dalloc(lp_problem* p, T** ptr, size_t count) {
   *ptr = nullptr;
   if (count == 0) count = 1;
+  const size_t bytes = (count * sizeof(T) + 255) / 256 * 256;
+  if (p->arena && bytes <= p->arena_size - p->arena_used) {
+    *ptr = reinterpret_cast<T*>(p->arena + p->arena_used);
+    p->arena_used += bytes;
+    return LP_OK;
+  }
   void* v = nullptr;
   cudaError_t e = cudaMalloc(&v, count * sizeof(T));
   if (e != cudaSuccess) {
@@ -221,17 +232,9 @@ int preprocess(lp_problem* p) {
   double* red = d.work + m + n;  // reduction scratch [1 + 1024]
   launch_fill(d.dr, 1.0, m, s);
   launch_fill(d.dc, 1.0, n, s);
-  auto apply = [&]() {
-    launch_factor_from_norm(fr, m, s);
-    launch_factor_from_norm(fc, n, s);
-    launch_scale_values(d.A_rp, d.A_ci, d.A_v, m, fr, fc, 1, s);
-    launch_scale_values(d.At_rp, d.At_ci, d.At_v, n, fr, fc, 0, s);
-    launch_mul_inplace(d.dr, fr, m, s);
-    launch_mul_inplace(d.dc, fc, n, s);
-  };
+  auto apply = [&]() { launch_ruiz_apply(d, p->split[0], p->split[1], fr, fc, s); };
   for (int r = 0; r < p->opt.ruiz_iters; ++r) {
-    launch_row_absmax(d.A, m, fr, s);
-    launch_row_absmax(d.At, n, fc, s);
+    launch_ruiz_norms(d, p->split[0], p->split[1], fr, fc, s);
     apply();
   }
   if (p->opt.mode == LP_MODE_PDLP) {
@@ -380,6 +383,13 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
     CK(cudaMemsetAsync(bt.ticket, 0, sizeof(unsigned int) * bt.seg_rows, p->stream));
     bt.seg_unit = su;
   }
+  for (int which = 0; which < 2; ++which) {
+    const std::vector<int>& rp = which ? lay.At_rp : lay.A_rp;
+    const int rows = which ? n : m;
+    int r = 0;
+    while (r < rows && rp[r + 1] - rp[r] > 32) ++r;
+    p->split[which] = r;
+  }
   for (int which = 0; which < 2; ++which) {  // sliced copies: filled on the device once the values are final
     const long long ns = sliced_entries(which ? d.binsAt : d.binsA);
     p->sell_n[which] = ns;
@@ -416,15 +426,17 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
     ts[i] = c0 == 'E' ? kEq : (c0 == 'L' ? kLe : kGe);
   }
   if (m > 0) CK(cudaMemcpyAsync(d.sense, ts.data(), m, cudaMemcpyHostToDevice, s));
-  for (int j = 0; j < n; ++j) tn[j] = c[lay.pcol[j]];
+  std::vector<double> tl(n), tu(n);
+  for (int j = 0; j < n; ++j) {
+    const int o = lay.pcol[j];
+    tn[j] = c[o];
+    tl[j] = lb[o];
+    tu[j] = ub[o];
+  }
   CK(cudaMemcpyAsync(d.f64.c, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  CK(cudaStreamSynchronize(s));  // tn is reused below
-  for (int j = 0; j < n; ++j) tn[j] = lb[lay.pcol[j]];
-  CK(cudaMemcpyAsync(d.f64.l, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  CK(cudaStreamSynchronize(s));
-  for (int j = 0; j < n; ++j) tn[j] = ub[lay.pcol[j]];
-  CK(cudaMemcpyAsync(d.f64.u, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpyAsync(d.f64.l, tl.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d.f64.u, tu.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the host buffers end with this function
   return LP_OK;
 }
 
@@ -603,6 +615,7 @@ void release(lp_problem* p) {
   for (auto e : p->events)
     if (e) cudaEventDestroy(e);
   for (void* v : p->allocs) cudaFree(v);
+  if (p->arena) cudaFree(p->arena);
   if (p->h_status) cudaFreeHost(p->h_status);
   if (p->h_scratch) cudaFreeHost(p->h_scratch);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -684,6 +697,18 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
   p->prm.alpha = o.alpha;
   p->prm.floor = o.precond_floor;
   p->prm.refine_tol = o.refine_tol;
+  {
+    int64_t bytes = 0;
+    if (lp_memory_bytes(m, n, lay.nnz, &o, &bytes) == LP_OK && bytes > 0) {
+      void* a = nullptr;
+      if (cudaMalloc(&a, (size_t)bytes) == cudaSuccess) {
+        p->arena = static_cast<char*>(a);
+        p->arena_size = (size_t)bytes;
+      } else {
+        cudaGetLastError();  // no room for one block: every buffer gets its own cudaMalloc
+      }
+    }
+  }
   if ((rc = upload(p, lay, b, c, lb, ub, sense)) != LP_OK) return fail(rc);
   if ((rc = preprocess(p)) != LP_OK) return fail(rc);
   if ((rc = create_events(p)) != LP_OK) return fail(rc);

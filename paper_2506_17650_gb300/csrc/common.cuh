@@ -424,12 +424,14 @@ int check_kernel_count();
 
 // setup
 void launch_fill(double* v, double val, long long n, cudaStream_t s);
-void launch_row_absmax(const Csr& M, int rows, double* out, cudaStream_t s);
+// Ruiz-style rounds on both CSR copies (rows of A and of A^T in bin order,
+// longest first; rows from split on have at most 32 entries):
+//   norms: fr = row infinity norms of A, fc = those of A^T (columns of A);
+//   apply: f <- f > 0 ? 1/sqrt(f) : 1 for fr and fc, dr *= fr, dc *= fc, and
+//          every entry a_ij <- (a_ij fr_i) fc_j in both copies.
+void launch_ruiz_norms(const Dev& d, int split_a, int split_at, double* fr, double* fc, cudaStream_t s);
+void launch_ruiz_apply(const Dev& d, int split_a, int split_at, double* fr, double* fc, cudaStream_t s);
 void launch_row_powsum(const Csr& M, int rows, double beta, int square_root, double* out, cudaStream_t s);
-void launch_factor_from_norm(double* f, int n, cudaStream_t s);  // f <- f > 0 ? 1/sqrt(f) : 1
-void launch_scale_values(int* rp, int* ci, double* v, int rows, const double* frow, const double* fcol,
-                         int row_is_a_row, cudaStream_t s);
-void launch_mul_inplace(double* a, const double* f, int n, cudaStream_t s);
 void launch_scale_problem_vectors(const Dev& d, cudaStream_t s);
 void launch_init_vectors(const Dev& d, cudaStream_t s);
 void launch_spmv_binned(const Csr& M, const BinTable& bt, int grid, const double* x, double* y, cudaStream_t s);

@@ -22,18 +22,6 @@ __global__ void fill_kernel(double* v, double val, long long n) {
     v[i] = val;
 }
 
-// one warp per row: out[r] = max_k |v_k|
-__global__ void row_absmax_kernel(Csr M, int rows, double* out) {
-  const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
-    double mx = 0.0;
-    for (int k = M.rp[r] + lane; k < M.rp[r + 1]; k += 32) mx = fmax(mx, fabs(M.v[k]));
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) out[r] = mx;
-  }
-}
-
 // one warp per row: out[r] = sum_k |v_k|^beta (beta == 1 and beta == 2 exact), optionally sqrt
 __global__ void row_powsum_kernel(Csr M, int rows, double beta, int square_root, double* out) {
   const int lane = threadIdx.x & 31;
@@ -49,32 +37,99 @@ __global__ void row_powsum_kernel(Csr M, int rows, double beta, int square_root,
   }
 }
 
-__global__ void factor_kernel(double* f, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double v = f[i];
-    f[i] = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+// Rows of one matrix in a Ruiz round: rows [0, split) -- the longer ones,
+// rows being sorted longest first -- take a warp each, rows [split, rows) (at
+// most 32 entries) a thread each.  Unit w of the matrix is warp row w for
+// w < split, else the 32 thread rows split + 32 (w - split) + lane.
+struct RuizRows {
+  const int* rp;
+  const int* ci;
+  double* v;
+  int rows;
+  int split;
+  __device__ __forceinline__ long long units() const { return split + (rows - split + 31) / 32; }
+};
+
+// out[r] = max_k |v_k| for the rows of unit w (max is exact: the result
+// does not depend on the order).
+__device__ __forceinline__ void absmax_unit(const RuizRows& R, long long w, int lane, double* out) {
+  if (w < R.split) {
+    const int r = (int)w;
+    double mx = 0.0;
+    for (int k = R.rp[r] + lane; k < R.rp[r + 1]; k += 32) mx = fmax(mx, fabs(R.v[k]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) out[r] = mx;
+  } else {
+    const long long r = R.split + (w - R.split) * 32 + lane;
+    if (r < R.rows) {
+      double mx = 0.0;
+      for (int k = R.rp[r]; k < R.rp[r + 1]; ++k) mx = fmax(mx, fabs(R.v[k]));
+      out[r] = mx;
+    }
   }
 }
 
 // v_k <- (v_k * frow_i) * fcol_j for entry (i, j) of A.  For the A copy the
 // row is i and ci is j; for the A^T copy the row is j and ci is i.  Both
 // copies evaluate the same expression, so they stay bitwise equal.
-__global__ void scale_values_kernel(const int* rp, const int* ci, double* v, int rows, const double* frow,
-                                    const double* fcol, int row_is_a_row) {
-  const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
-    for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) {
-      const int c = ci[k];
-      const int i = row_is_a_row ? r : c;
-      const int j = row_is_a_row ? c : r;
-      v[k] = (v[k] * frow[i]) * fcol[j];
-    }
+__device__ __forceinline__ void scale_unit(const RuizRows& R, long long w, int lane, const double* frow,
+                                           const double* fcol, bool a_rows) {
+  long long r, k0, k1;
+  int step;
+  if (w < R.split) {
+    r = w;
+    k0 = R.rp[r] + lane;
+    step = 32;
+  } else {
+    r = R.split + (w - R.split) * 32 + lane;
+    if (r >= R.rows) return;
+    k0 = R.rp[r];
+    step = 1;
+  }
+  k1 = R.rp[r + 1];
+  for (long long k = k0; k < k1; k += step) {
+    const int c = R.ci[k];
+    const long long i = a_rows ? r : c;
+    const long long j = a_rows ? c : r;
+    R.v[k] = (R.v[k] * frow[i]) * fcol[j];
   }
 }
 
-__global__ void mul_kernel(double* a, const double* f, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] *= f[i];
+// Row infinity norms of A (into fr) and of A^T (column norms of A, into fc),
+// one launch for both.
+__global__ void ruiz_norms_kernel(RuizRows A, RuizRows At, double* fr, double* fc) {
+  const int lane = threadIdx.x & 31;
+  const long long ua = A.units(), total = ua + At.units();
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+    if (w < ua) absmax_unit(A, w, lane, fr);
+    else absmax_unit(At, w - ua, lane, fc);
+  }
+}
+
+// Both CSR copies scaled by the row factors fr and column factors fc.
+__global__ void ruiz_scale_kernel(RuizRows A, RuizRows At, const double* fr, const double* fc) {
+  const int lane = threadIdx.x & 31;
+  const long long ua = A.units(), total = ua + At.units();
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+    if (w < ua) scale_unit(A, w, lane, fr, fc, true);
+    else scale_unit(At, w - ua, lane, fr, fc, false);
+  }
+}
+
+// Norms -> factors f = 1 / sqrt(norm) (1 for an empty row or column), and the
+// accumulated scalings dr *= f_row, dc *= f_col.
+__global__ void factor_mul_kernel(double* fr, double* dr, int m, double* fc, double* dc, int n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)m + n;
+       t += (long long)gridDim.x * blockDim.x) {
+    double* f = t < m ? fr + t : fc + (t - m);
+    double* acc = t < m ? dr + t : dc + (t - m);
+    const double v = *f;
+    const double g = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+    *f = g;
+    *acc *= g;
+  }
 }
 
 __global__ void scale_vectors_kernel(Dev d) {
@@ -290,25 +345,28 @@ void launch_fill(double* v, double val, long long n, cudaStream_t s) {
   if (n > 0) fill_kernel<<<grid_for(n), kBlock, 0, s>>>(v, val, n);
 }
 
-void launch_row_absmax(const Csr& M, int rows, double* out, cudaStream_t s) {
-  if (rows > 0) row_absmax_kernel<<<warp_grid_for(rows), kBlock, 0, s>>>(M, rows, out);
-}
 
 void launch_row_powsum(const Csr& M, int rows, double beta, int square_root, double* out, cudaStream_t s) {
   if (rows > 0) row_powsum_kernel<<<warp_grid_for(rows), kBlock, 0, s>>>(M, rows, beta, square_root, out);
 }
 
-void launch_factor_from_norm(double* f, int n, cudaStream_t s) {
-  if (n > 0) factor_kernel<<<grid_for(n), kBlock, 0, s>>>(f, n);
+namespace {
+RuizRows ruiz_rows(int* rp, int* ci, double* v, int rows, int split) { return RuizRows{rp, ci, v, rows, split}; }
+int ruiz_grid(const Dev& d, int split_a, int split_at) {
+  const long long units = split_a + (d.m - split_a + 31) / 32 + split_at + (d.n - split_at + 31) / 32;
+  return warp_grid_for(units);
+}
+}  // namespace
+
+void launch_ruiz_norms(const Dev& d, int split_a, int split_at, double* fr, double* fc, cudaStream_t s) {
+  ruiz_norms_kernel<<<ruiz_grid(d, split_a, split_at), kBlock, 0, s>>>(
+      ruiz_rows(d.A_rp, d.A_ci, d.A_v, d.m, split_a), ruiz_rows(d.At_rp, d.At_ci, d.At_v, d.n, split_at), fr, fc);
 }
 
-void launch_scale_values(int* rp, int* ci, double* v, int rows, const double* frow, const double* fcol,
-                         int row_is_a_row, cudaStream_t s) {
-  if (rows > 0) scale_values_kernel<<<warp_grid_for(rows), kBlock, 0, s>>>(rp, ci, v, rows, frow, fcol, row_is_a_row);
-}
-
-void launch_mul_inplace(double* a, const double* f, int n, cudaStream_t s) {
-  if (n > 0) mul_kernel<<<grid_for(n), kBlock, 0, s>>>(a, f, n);
+void launch_ruiz_apply(const Dev& d, int split_a, int split_at, double* fr, double* fc, cudaStream_t s) {
+  factor_mul_kernel<<<grid_for((long long)d.m + d.n), kBlock, 0, s>>>(fr, d.dr, d.m, fc, d.dc, d.n);
+  ruiz_scale_kernel<<<ruiz_grid(d, split_a, split_at), kBlock, 0, s>>>(
+      ruiz_rows(d.A_rp, d.A_ci, d.A_v, d.m, split_a), ruiz_rows(d.At_rp, d.At_ci, d.At_v, d.n, split_at), fr, fc);
 }
 
 void launch_scale_problem_vectors(const Dev& d, cudaStream_t s) {

@@ -354,6 +354,31 @@ def test_unsorted_rows_and_repeated_entries_give_the_same_solve():
     assert out[0]["eta"] == out[1]["eta"] and out[0]["omega"] == out[1]["omega"]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_device_memory_of_a_problem_within_lp_memory_bytes(precision):
+    """lp_create takes its device buffers from one allocation of the
+    lp_memory_bytes bound: the device's free memory drops by about that much
+    (whole 2 MiB pages, plus the stream and graph) and no more."""
+    torch = pytest.importorskip("torch")
+    prec = lpop.LP_PREC_FP64 if precision == "fp64" else lpop.LP_PREC_MIXED
+    lp = lpgen.transport(0, 5000, 5000, 80000)
+    with lpop.Problem(lp, precision=prec) as warm:  # library, kernels and per-device tables loaded
+        warm.solve(1e-4, 2000)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    bound = lpop.lp_memory_bytes(lp.m, lp.n, lp.nnz, lpop.lp_options_default(precision=prec))
+    p = lpop.Problem(lp, precision=prec)
+    try:
+        p.solve(1e-4, 2000)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        used = free0 - free1
+        assert used <= bound + (8 << 20), (used, bound)
+        assert used >= bound - (4 << 20), (used, bound)
+    finally:
+        p.close()
+
+
 def test_alpha_zero_keeps_identity_preconditioners():
     lp = lpgen.mixed_small(4)
     o = oracle.Options(alpha=0.0, phi=1)
