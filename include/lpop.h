@@ -322,8 +322,10 @@ void lp_batch_destroy(lp_batch* b);
 
 /* Device bytes lp_create allocates for a problem of this size with these
  * options (after merging repeated entries nnz can only shrink), for callers
- * that admit problems by free memory.  Writes *bytes; LP_ERR_INVALID_ARG on
- * bad sizes or NULL bytes. */
+ * that admit problems by free memory: lp_create takes all of a problem's
+ * device buffers from one allocation of this size (the per-device step-size
+ * table, 16 MiB, is shared by all problems on a device and not included).
+ * Writes *bytes; LP_ERR_INVALID_ARG on bad sizes or NULL bytes. */
 int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, int64_t* bytes);
 
 /* Free all device and host memory of the problem.  NULL is ignored. */

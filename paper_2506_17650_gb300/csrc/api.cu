@@ -1032,7 +1032,7 @@ int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, in
   lp_options o;
   if (opt) o = *opt;
   else lp_options_default(&o);
-  // mirrors upload(): each cudaMalloc is rounded up to 256 bytes
+  // mirrors upload(): every buffer is a 256-byte multiple of the block lp_create allocates
   auto r = [](long long b) { return ((b < 8 ? 8 : b) + 255) / 256 * 256; };
   long long t = 0;
   t += r(4LL * (m + 1)) + 2 * r(4LL * nnz) + 2 * r(8LL * nnz) + r(4LL * (n + 1));  // CSR of A and A^T
