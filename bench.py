@@ -293,7 +293,9 @@ def gpu_arm(args):
 
     lp = make_lp(kind, args.scale)
     stream = torch.cuda.Stream()
-    opts = dict(alpha=ALPHA, phi=PHI, normalize=1, kernel_timing=1, device=local, stream=stream.cuda_stream)
+    # kernel timing: CUDA events around the two step kernels of one attempt in 32
+    # (each event node breaks the programmatic-launch overlap of its neighbours)
+    opts = dict(alpha=ALPHA, phi=PHI, normalize=1, kernel_timing=32, device=local, stream=stream.cuda_stream)
     prob = lpop.Problem(lp, **opts)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     _, _, layout = prob.scaling()

@@ -93,7 +93,8 @@ typedef struct lp_options {
   double plain_step_factor;  /* plain mode step = factor / ||A~||_2; default 0.9 */
   double time_limit;         /* seconds per lp_solve call; <= 0 means none; default 0 */
   int32_t use_graph;         /* replay one check period as a CUDA graph; default 1 */
-  int32_t kernel_timing;     /* time sampled launches of the hot kernels with CUDA events; default 0 */
+  int32_t kernel_timing;     /* time sampled launches of the hot kernels with CUDA events: 0 off (default),
+                                1 one attempt in 8, k >= 2 one attempt in k of each check period */
   int32_t device;            /* CUDA device ordinal; -1 = the calling thread's current device */
   void* stream;              /* cudaStream_t every launch and copy goes to; NULL = default stream */
   int32_t precision;         /* LP_PREC_*; default LP_PREC_FP64 */
@@ -214,7 +215,7 @@ int lp_set_state(lp_problem* p, const double* vec_n, const double* vec_m, const 
 int lp_reset(lp_problem* p);
 
 /*
- * Kernel timing (options.kernel_timing = 1): accumulated CUDA-event time in
+ * Kernel timing (options.kernel_timing >= 1): accumulated CUDA-event time in
  * milliseconds and sample counts of the sampled launches, for up to n_kernels
  * kernels in the order {primal step, dual step}.  launches (may be NULL)
  * receives the number of kernel launches issued since create/reset.

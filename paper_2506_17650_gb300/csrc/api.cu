@@ -164,6 +164,7 @@ int check_options(const lp_options& o, std::string& msg) {
   if (o.power_iters < 1) return msg = "power_iters must be >= 1", 1;
   if (!(o.plain_step_factor > 0.0)) return msg = "plain_step_factor must be > 0", 1;
   if (o.precision != LP_PREC_FP64 && o.precision != LP_PREC_MIXED) return msg = "unknown precision", 1;
+  if (o.kernel_timing < 0) return msg = "kernel_timing must be >= 0", 1;
   if (!(o.refine_tol >= 0.0)) return msg = "refine_tol must be >= 0", 1;
   for (int i = 0; i < 8; ++i)
     if (o.reserved[i] != 0) return msg = "reserved option fields must be zero", 1;
@@ -440,15 +441,18 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
   return LP_OK;
 }
 
+// Attempts per timed sample: kernel_timing 1 times one attempt in 8, k >= 2 one in k.
+int timing_stride(const lp_problem* p) { return p->opt.kernel_timing == 1 ? 8 : p->opt.kernel_timing; }
+
 int create_events(lp_problem* p) {
   if (!p->opt.kernel_timing) return LP_OK;
-  p->samples = (p->opt.check_every + 7) / 8;
+  p->samples = (p->opt.check_every + timing_stride(p) - 1) / timing_stride(p);
   p->events.resize(3 * p->samples, nullptr);
   for (auto& e : p->events) CK(cudaEventCreate(&e));
   return LP_OK;
 }
 
-bool sampled(const lp_problem* p, int a) { return p->opt.kernel_timing && (a % 8) == 0; }
+bool sampled(const lp_problem* p, int a) { return p->opt.kernel_timing && (a % timing_stride(p)) == 0; }
 
 int capture_graph(lp_problem* p, bool fp32) {
   cudaGraphExec_t* slot = fp32 ? &p->gexec32 : &p->gexec;
@@ -458,7 +462,7 @@ int capture_graph(lp_problem* p, bool fp32) {
   const int ce = p->opt.check_every;
   for (int a = 0; a < ce; ++a) {
     const bool tm = sampled(p, a);
-    const int sidx = a / 8;
+    const int sidx = a / (p->opt.kernel_timing ? timing_stride(p) : 1);
     if (tm) cudaEventRecordWithFlags(p->events[3 * sidx], p->stream, cudaEventRecordExternal);
     launch_primal(p->d, p->prm, fp32, p->stream);
     if (tm) cudaEventRecordWithFlags(p->events[3 * sidx + 1], p->stream, cudaEventRecordExternal);

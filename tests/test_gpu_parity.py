@@ -436,6 +436,12 @@ def test_kernel_timing_and_launch_count():
     assert ms[0] > 0 and ms[1] > 0
     # initial check (3 launches) + 4 graph replays of 64 attempts (2 kernels each) and a check (3)
     assert launches == 3 + 4 * (2 * 64 + 3)
+    assert samples[0] == samples[1] == 4 * 64 // 8  # one attempt in 8 of each replay
+    with lpop.Problem(lp, **gpu_options(o, kernel_timing=32)) as p:
+        p.solve(0.0, 256)
+        ms32, samples32, _ = p.kernel_times()
+    assert samples32[0] == samples32[1] == 4 * 64 // 32
+    assert ms32[0] > 0 and ms32[1] > 0
 
 
 def test_invalid_input_rejected_before_device_work():
