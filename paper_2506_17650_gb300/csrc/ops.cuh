@@ -165,47 +165,92 @@ struct DualOp {
 // Sigma^-1 weighted norms, next step size, buffer swap, online-update scalars.
 // Works on a copy of the state held by the caller.
 // f1, f2: step_factors() of attempt s.attempts + 1.
-__device__ inline void step_control_state(DevState& s, const Params& prm, double f1, double f2,
-                                          const double (&t1)[3], const double (&t2)[4]) {
-  const double eta = s.eta, omega = s.omega;
-  const bool collect = s.collect;
+//
+// It runs once per attempt in one thread of one block, so it is written for
+// latency on GB300, where a dependent FP64 operation takes ~64 cycles, an
+// FP64 min ~160 and a division ~550, and where the code runs with cold
+// instruction caches: comparisons and the min are done on the integer bits
+// of the (non-negative) operands, the mode is a template parameter, and the
+// online-update scalars (once every phi accepted attempts) are set out of line.
+
+// Bits of a double that is NaN (any sign).
+__device__ __forceinline__ bool nan_bits(long long b) { return (b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL; }
+
+// Accepted attempt that records q / p: scalars of the pending update of T and
+// Sigma (Eq. (7), Algorithm 1; normalised by ||g||^2 and ||b - A x||^2).
+__device__ __noinline__ void control_collect(DevState& s, int normalize, int sched, double eta, double omega,
+                                             double inv_omega, double gp2, double q2, double rd2, double p2) {
+  s.pend_p = 0;
+  s.pend_d = 0;
+  if (!normalize || gp2 > 0.0) {
+    const double sc = -(eta * inv_omega) * (normalize ? 1.0 / gp2 : 1.0);
+    s.up_scale_p = sc;
+    s.pend_p = 1;
+    if (sched == kAdagradNorm) s.gp_norm += sc * sc * q2;
+  }
+  if (!normalize || rd2 > 0.0) {
+    const double sc = -(eta * omega) * (normalize ? 1.0 / rd2 : 1.0);
+    s.up_scale_d = sc;
+    s.pend_d = 1;
+    if (sched == kAdagradNorm) s.gd_norm += sc * sc * p2;
+  }
+  if (sched == kAdagradNorm) {
+    s.sqrt_gp = s.gp_norm > 0.0 ? sqrt(s.gp_norm) : 0.0;
+    s.sqrt_gd = s.gd_norm > 0.0 ? sqrt(s.gd_norm) : 0.0;
+  }
+}
+
+template <bool Pdlp>
+__device__ inline void step_control_t(DevState& s, const Params& prm, double f1, double f2, const double (&t1)[3],
+                                      const double (&t2)[4]) {
+  const double eta = s.eta, omega = s.omega, inv_omega = s.inv_omega;
+  const int collect = s.collect;
+  bool accept = true;
+  double eta_next = eta;
+  if (Pdlp) {
+    const double movement = omega * t1[0] + t2[0] * inv_omega;
+    const double interaction = fabs(t2[1]);
+    // interaction > 0 (NaN excluded)
+    const long long ib = __double_as_longlong(interaction);
+    const double eta_max = (ib > 0 && ib <= 0x7ff0000000000000LL) ? movement / (2.0 * interaction) : INFINITY;
+    // eta <= eta_max (both >= 0; false for NaN)
+    const long long mb = __double_as_longlong(eta_max);
+    accept = !nan_bits(mb) && __double_as_longlong(eta) <= mb;
+    // fmin(f1 eta_max, f2 eta) (both >= 0)
+    const double a = f1 * eta_max, b = f2 * eta;
+    const long long ab = __double_as_longlong(a), bb = __double_as_longlong(b);
+    eta_next = nan_bits(ab) ? b : (nan_bits(bb) ? a : (ab < bb ? a : b));
+    s.last_eta_max = eta_max;
+  }
+  const int k_mod_next = s.k_mod + 1 == prm.phi ? 0 : s.k_mod + 1;
   s.pend_p = 0;  // applied by this attempt's kernels
   s.pend_d = 0;
   s.attempts += 1;
-  bool accept = true;
-  double eta_next = eta;
-  if (prm.mode == kPdlp) {
-    const double movement = omega * t1[0] + t2[0] * s.inv_omega;
-    const double interaction = fabs(t2[1]);
-    const double eta_max = interaction > 0.0 ? movement / (2.0 * interaction) : INFINITY;
-    accept = eta <= eta_max;
-    eta_next = fmin(f1 * eta_max, f2 * eta);
-    s.last_eta_max = eta_max;
-  }
   if (accept) {
-    if (collect) {
-      if (!prm.normalize || t1[1] > 0.0) {
-        const double sc = -(eta * s.inv_omega) * (prm.normalize ? 1.0 / t1[1] : 1.0);
-        s.up_scale_p = sc;
-        s.pend_p = 1;
-        if (prm.sched == kAdagradNorm) s.gp_norm += sc * sc * t1[2];
-      }
-      if (!prm.normalize || t2[2] > 0.0) {
-        const double sc = -(eta * omega) * (prm.normalize ? 1.0 / t2[2] : 1.0);
-        s.up_scale_d = sc;
-        s.pend_d = 1;
-        if (prm.sched == kAdagradNorm) s.gd_norm += sc * sc * t2[3];
-      }
-    }
-    if (prm.mode == kPdlp) s.wsum += eta;
+    if (Pdlp) s.wsum += eta;
     s.cur ^= 1;
     s.k += 1;
-    if (prm.phi > 0) s.k_mod = s.k_mod + 1 == prm.phi ? 0 : s.k_mod + 1;
+    if (prm.phi > 0) s.k_mod = k_mod_next;
   }
   s.eta = eta_next;
   s.last_accept = accept ? 1 : 0;
   s.counter = 0;
-  refresh_derived(s, prm.phi, prm.sched);
+  // derived scalars (refresh_derived); the square roots of the AdaGrad-norm
+  // sums change only where the sums do (control_collect)
+  s.collect = prm.phi > 0 && s.k_mod == 0;
+  s.step_p = eta_next * inv_omega;
+  s.step_d = eta_next * omega;
+  if (prm.sched != kAdagradNorm) {
+    s.sqrt_gp = 0.0;
+    s.sqrt_gd = 0.0;
+  }
+  if (accept && collect) control_collect(s, prm.normalize, prm.sched, eta, omega, inv_omega, t1[1], t1[2], t2[2], t2[3]);
+}
+
+__device__ inline void step_control_state(DevState& s, const Params& prm, double f1, double f2,
+                                          const double (&t1)[3], const double (&t2)[4]) {
+  if (prm.mode == kPdlp) step_control_t<true>(s, prm, f1, f2, t1, t2);
+  else step_control_t<false>(s, prm, f1, f2, t1, t2);
 }
 
 // Vectors of type V (FP64, or FP32 in the mixed-precision phase); every
