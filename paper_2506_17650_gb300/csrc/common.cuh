@@ -219,7 +219,7 @@ __device__ inline void block_sum(T (&v)[N], T* smem /* [32 * N] */) {
 }
 
 // Block sum through shared memory: every thread stores its N values, then one
-// warp adds them (8 per lane, then a shuffle tree).  Far fewer FP64
+// warp adds them (8 per lane as a pairwise tree, then a shuffle tree).  Far fewer FP64
 // instructions than a shuffle tree in every warp.  Result valid in thread 0.
 // smem must hold N * blockDim.x doubles; blockDim.x must be 256.
 template <int N>
@@ -231,9 +231,11 @@ __device__ inline void block_sum_smem(double (&v)[N], double* smem) {
   if (tid < 32) {
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-      double t = smem[q * 256 + tid];
+      double a[8];
 #pragma unroll
-      for (int k = 1; k < 8; ++k) t += smem[q * 256 + tid + 32 * k];
+      for (int k = 0; k < 8; ++k) a[k] = smem[q * 256 + tid + 32 * k];
+      // pairwise (depth 3, the same 7 adds as a chain)
+      double t = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
       v[q] = t;
