@@ -1,9 +1,9 @@
-// Test driver for the library's host-side layout code (csrc/host_layout.cpp):
+// Test program for the library's host-side layout code (csrc/host_layout.cpp):
 // reads a CSR matrix from three raw files, runs build_layout (and optionally
 // segment_long_rows on both bin tables), and writes everything it produced to
 // one raw file that tests/test_host_layout.py reads back and checks.
 //
-//   host_layout_driver m n nnz in_prefix out_path target_threads seg_len
+//   host_layout_runner m n nnz in_prefix out_path target_threads seg_len
 //
 // Input files: <in_prefix>rp.bin (int64 [m+1]), ci.bin (int32 [nnz]),
 // v.bin (float64 [nnz]).  seg_len <= 0 skips the segmentation.

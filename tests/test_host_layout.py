@@ -1,6 +1,6 @@
 """Host-side layout of a problem (csrc/host_layout.cpp), checked on the CPU.
 
-tests/host_layout_driver.cpp runs the library's build_layout (and
+tests/host_layout_runner.cpp runs the library's build_layout (and
 segment_long_rows) on a CSR matrix; these tests check what it produced
 against scipy.sparse and against the layout's own definition:
 
@@ -30,12 +30,12 @@ K_SEGMENTED, K_SELL, K_BLOCK = -1, -2, 256
 
 
 @pytest.fixture(scope="module")
-def driver(tmp_path_factory):
+def runner(tmp_path_factory):
     gxx = shutil.which("g++")
     if gxx is None:
         pytest.skip("g++ not available")
-    out = str(tmp_path_factory.mktemp("layout") / "host_layout_driver")
-    subprocess.run([gxx, "-O1", "-std=c++17", "-pthread", "-I", CSRC, os.path.join(ROOT, "tests", "host_layout_driver.cpp"),
+    out = str(tmp_path_factory.mktemp("layout") / "host_layout_runner")
+    subprocess.run([gxx, "-O1", "-std=c++17", "-pthread", "-I", CSRC, os.path.join(ROOT, "tests", "host_layout_runner.cpp"),
                     os.path.join(CSRC, "host_layout.cpp"), "-o", out], check=True, capture_output=True)
     return out
 
@@ -62,13 +62,13 @@ class _Reader:
                     bins=[dict(zip(("row_begin", "row_end", "width", "unit_begin", "len", "base"), r)) for r in rows])
 
 
-def run_layout(driver, tmp_path, m, n, rp, ci, v, target=0, seg_len=0):
+def run_layout(runner, tmp_path, m, n, rp, ci, v, target=0, seg_len=0):
     pre = str(tmp_path / "in_")
     np.asarray(rp, np.int64).tofile(pre + "rp.bin")
     np.asarray(ci, np.int32).tofile(pre + "ci.bin")
     np.asarray(v, np.float64).tofile(pre + "v.bin")
     out = str(tmp_path / "out.bin")
-    subprocess.run([driver, str(m), str(n), str(len(ci)), pre, out, str(target), str(seg_len)], check=True)
+    subprocess.run([runner, str(m), str(n), str(len(ci)), pre, out, str(target), str(seg_len)], check=True)
     r = _Reader(open(out, "rb").read())
     rc = r.take("<i")
     n_err = r.take("<i")
@@ -169,18 +169,18 @@ CASES = {
 
 @pytest.mark.parametrize("case", sorted(CASES))
 @pytest.mark.parametrize("target", [0, 1 << 20])
-def test_layout_is_the_permuted_matrix_and_its_transpose(driver, tmp_path, case, target):
+def test_layout_is_the_permuted_matrix_and_its_transpose(runner, tmp_path, case, target):
     lp = CASES[case]()
-    lay = run_layout(driver, tmp_path, lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, target=target)
+    lay = run_layout(runner, tmp_path, lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, target=target)
     check_layout(lay, lp.m, lp.n, lp.csr())
 
 
 @pytest.mark.parametrize("case", ["transport", "rowmix", "long_rows"])
-def test_shuffled_rows_and_repeated_entries_give_the_same_layout(driver, tmp_path, case):
+def test_shuffled_rows_and_repeated_entries_give_the_same_layout(runner, tmp_path, case):
     lp = CASES[case]()
-    clean = run_layout(driver, tmp_path, lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val)
+    clean = run_layout(runner, tmp_path, lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val)
     rp, ci, v = messy(lp, 3)
-    lay = run_layout(driver, tmp_path, lp.m, lp.n, rp, ci, v)
+    lay = run_layout(runner, tmp_path, lp.m, lp.n, rp, ci, v)
     ref = sp.csr_matrix((v, ci, rp), shape=(lp.m, lp.n))
     ref.sum_duplicates()
     check_layout(lay, lp.m, lp.n, ref)
@@ -188,10 +188,10 @@ def test_shuffled_rows_and_repeated_entries_give_the_same_layout(driver, tmp_pat
         assert np.array_equal(lay[key], clean[key]), key
 
 
-def test_segmentation_cuts_exactly_the_long_rows(driver, tmp_path):
+def test_segmentation_cuts_exactly_the_long_rows(runner, tmp_path):
     lp = lpgen.long_rows(0)
     seg_len = 4096
-    lay = run_layout(driver, tmp_path, lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, seg_len=seg_len)
+    lay = run_layout(runner, tmp_path, lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, seg_len=seg_len)
     for rp_key, bt_key, seg_key in (("A_rp", "binsA", "segA"), ("At_rp", "binsAt", "segAt")):
         rp, bt, units = lay[rp_key], lay[bt_key], lay[seg_key].reshape(-1, 2)
         lens = np.diff(rp)
@@ -215,7 +215,7 @@ def test_segmentation_cuts_exactly_the_long_rows(driver, tmp_path):
     ("rowptr_dec", "row_ptr must be non-decreasing (row 2)"),
     ("rowptr_end", "row_ptr[0] must be 0 and row_ptr[m] must equal nnz"),
 ])
-def test_invalid_input_names_the_first_offending_entry(driver, tmp_path, what, expect):
+def test_invalid_input_names_the_first_offending_entry(runner, tmp_path, what, expect):
     lp = lpgen.mixed_small(0, m=12, n=20)
     rp, ci, v = lp.row_ptr.copy(), lp.col_idx.copy(), lp.val.copy()
     if what == "col_high":
@@ -233,12 +233,12 @@ def test_invalid_input_names_the_first_offending_entry(driver, tmp_path, what, e
         rp[3] = rp[2] - 1
     elif what == "rowptr_end":
         rp[-1] += 1  # one more entry than the arrays hold
-    lay = run_layout(driver, tmp_path, lp.m, lp.n, rp, ci, v)
+    lay = run_layout(runner, tmp_path, lp.m, lp.n, rp, ci, v)
     assert lay["rc"] < 0 and lay["err"] == expect
 
 
-def test_empty_rows_and_no_constraints(driver, tmp_path):
-    lay = run_layout(driver, tmp_path, 0, 5, [0], [], [])
+def test_empty_rows_and_no_constraints(runner, tmp_path):
+    lay = run_layout(runner, tmp_path, 0, 5, [0], [], [])
     assert lay["rc"] == 0 and lay["nnz"] == 0 and sorted(lay["pcol"]) == list(range(5))
-    lay = run_layout(driver, tmp_path, 4, 3, [0, 0, 2, 2, 3], [2, 0, 1], [1.0, 2.0, 3.0])
+    lay = run_layout(runner, tmp_path, 4, 3, [0, 0, 2, 2, 3], [2, 0, 1], [1.0, 2.0, 3.0])
     check_layout(lay, 4, 3, sp.csr_matrix(([1.0, 2.0, 3.0], [2, 0, 1], [0, 0, 2, 2, 3]), shape=(4, 3)))
