@@ -87,7 +87,8 @@ typedef struct lp_options {
   double precond_floor;      /* projection floor for T and Sigma; default 1e-6 */
   int32_t ruiz_iters;        /* Ruiz rounds (Section 2); default 10 */
   double pc_beta;            /* Pock-Chambolle exponent beta in [0, 2] (pdlp mode); default 1 */
-  int32_t check_every;       /* attempts between KKT / restart checks; default 64 */
+  int32_t check_every;       /* attempts between KKT / restart checks, 1..65536 (one check period is
+                                captured as one CUDA graph); default 64 */
   int32_t restart;           /* adaptive restarts in pdlp mode; default 1 */
   int32_t power_iters;       /* power iterations for ||A~||_2 (plain mode); default 200 */
   double plain_step_factor;  /* plain mode step = factor / ||A~||_2; default 0.9 */

@@ -160,7 +160,7 @@ int check_options(const lp_options& o, std::string& msg) {
   if (!(o.precond_floor > 0.0) || !std::isfinite(o.precond_floor)) return msg = "precond_floor must be > 0", 1;
   if (o.ruiz_iters < 0 || o.ruiz_iters > 1000) return msg = "ruiz_iters must be in [0, 1000]", 1;
   if (!(o.pc_beta >= 0.0 && o.pc_beta <= 2.0)) return msg = "pc_beta must be in [0, 2]", 1;
-  if (o.check_every < 1) return msg = "check_every must be >= 1", 1;
+  if (o.check_every < 1 || o.check_every > (1 << 16)) return msg = "check_every must be in [1, 65536]", 1;
   if (o.power_iters < 1) return msg = "power_iters must be >= 1", 1;
   if (!(o.plain_step_factor > 0.0)) return msg = "plain_step_factor must be > 0", 1;
   if (o.precision != LP_PREC_FP64 && o.precision != LP_PREC_MIXED) return msg = "unknown precision", 1;
@@ -446,7 +446,7 @@ int timing_stride(const lp_problem* p) { return p->opt.kernel_timing == 1 ? 8 : 
 
 int create_events(lp_problem* p) {
   if (!p->opt.kernel_timing) return LP_OK;
-  p->samples = (p->opt.check_every + timing_stride(p) - 1) / timing_stride(p);
+  p->samples = (p->opt.check_every - 1) / timing_stride(p) + 1;  // attempts 0, stride, ... of a period
   p->events.resize(3 * p->samples, nullptr);
   for (auto& e : p->events) CK(cudaEventCreate(&e));
   return LP_OK;
