@@ -31,6 +31,7 @@
 #ifndef LPOP_H
 #define LPOP_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -78,6 +79,16 @@ enum {
   LP_SCHED_CONST = 2         /* constant learning rate */
 };
 
+/* Optional allocator for a problem's device buffers, for callers whose device
+ * memory belongs to a framework (for example a caching allocator).  alloc
+ * returns at least `bytes` bytes of device memory on the problem's device,
+ * aligned to 256 bytes, or NULL (lp_create then fails with LP_ERR_OOM); free
+ * returns a block alloc gave, with the same size.  Both are called only from
+ * lp_create and lp_destroy, on the calling thread; lp_destroy synchronises the
+ * problem's stream before it frees. */
+typedef void* (*lp_device_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*lp_device_free_fn)(void* ptr, size_t bytes, void* ctx);
+
 typedef struct lp_options {
   int32_t mode;              /* LP_MODE_*; default LP_MODE_PDLP */
   int32_t scheduler;         /* LP_SCHED_*; default LP_SCHED_ADAGRAD */
@@ -102,7 +113,12 @@ typedef struct lp_options {
   double refine_tol;         /* mixed: the FP32 phase hands over to FP64 once the relative KKT
                                 error is at most this, or after 3 checks without a 10% gain;
                                 default 1e-6 */
-  int32_t reserved[8];       /* must be zero */
+  lp_device_alloc_fn device_alloc; /* NULL: cudaMalloc.  A problem takes its buffers from one block of
+                                      lp_memory_bytes() bytes (the per-device step-size table, 16 MiB,
+                                      shared by all problems, always comes from cudaMalloc) */
+  lp_device_free_fn device_free;   /* required exactly when device_alloc is set */
+  void* alloc_ctx;                 /* passed to device_alloc and device_free */
+  int32_t reserved[2];             /* must be zero */
 } lp_options;
 
 typedef struct lp_stats {

@@ -62,7 +62,10 @@ class LpOptions(ctypes.Structure):
         ("stream", c_void_p),
         ("precision", c_int32),
         ("refine_tol", c_double),
-        ("reserved", c_int32 * 8),
+        ("device_alloc", c_void_p),
+        ("device_free", c_void_p),
+        ("alloc_ctx", c_void_p),
+        ("reserved", c_int32 * 2),
     ]
 
 
@@ -322,14 +325,50 @@ def lp_last_error(handle=None) -> str:
     return msg.decode() if msg else ""
 
 
+_DEVICE_ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, ctypes.c_size_t, c_void_p)
+_DEVICE_FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, ctypes.c_size_t, c_void_p)
+
+
+class TorchDeviceAllocator:
+    """lp_options.device_alloc / device_free backed by PyTorch's caching
+    allocator: a problem's device buffers then count against (and come back
+    to) torch's memory pool.  Keep the object alive as long as the problems
+    that use it (Problem does)."""
+
+    def __init__(self, device=None):
+        import torch
+
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._alloc = _DEVICE_ALLOC_FN(self._do_alloc)
+        self._free = _DEVICE_FREE_FN(self._do_free)
+
+    def _do_alloc(self, nbytes, ctx):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device)
+        except RuntimeError:
+            return None  # the library reports LP_ERR_OOM
+
+    def _do_free(self, ptr, nbytes, ctx):
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+    def options(self):
+        return dict(device_alloc=ctypes.cast(self._alloc, c_void_p).value,
+                    device_free=ctypes.cast(self._free, c_void_p).value)
+
+
 class Problem:
     """Owning wrapper: ``with Problem(lp, alpha=1e-3) as p: p.solve(1e-4)``.
 
     ``lp`` is any object with the attributes m, n, row_ptr, col_idx, val, b,
-    c, lb, ub, sense (the caller's host arrays)."""
+    c, lb, ub, sense (the caller's host arrays).  ``allocator``: an object with
+    ``options()`` giving device_alloc / device_free (e.g. TorchDeviceAllocator)."""
 
-    def __init__(self, lp, **options):
+    def __init__(self, lp, allocator=None, **options):
         self.m, self.n = int(lp.m), int(lp.n)
+        self.allocator = allocator  # its callbacks must outlive the problem
+        if allocator is not None:
+            options = dict(options, **allocator.options())
         self.options = lp_options_default(**options)
         self.handle = lp_create(self.m, self.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, lp.lb, lp.ub,
                                 lp.sense, self.options)

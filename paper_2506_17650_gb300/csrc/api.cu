@@ -61,10 +61,12 @@ struct lp_problem {
   int* h_status = nullptr;  // pinned
   double* h_scratch = nullptr;  // pinned, 8 doubles
   // device memory: one allocation of the lp_memory_bytes bound, handed out
-  // by dalloc in 256-byte steps; anything beyond it gets its own cudaMalloc
+  // by dalloc in 256-byte steps; anything beyond it gets its own allocation
+  // (cudaMalloc, or the caller's device_alloc with its size kept for device_free)
   char* arena = nullptr;
   size_t arena_size = 0, arena_used = 0;
   std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> ext_allocs;
   // sliced copies of the kSell bins of A (0) and A^T (1): entries, column
   // indices and values, filled on the device once the preprocessed values
   // are final
@@ -136,6 +138,13 @@ int dalloc(lp_problem* p, T** ptr, size_t count) {
     return LP_OK;
   }
   void* v = nullptr;
+  if (p->opt.device_alloc) {
+    v = p->opt.device_alloc(bytes, p->opt.alloc_ctx);
+    if (!v) return set_err(p, LP_ERR_OOM, "device_alloc of " + std::to_string(bytes) + " bytes returned NULL");
+    p->ext_allocs.emplace_back(v, bytes);
+    *ptr = static_cast<T*>(v);
+    return LP_OK;
+  }
   cudaError_t e = cudaMalloc(&v, count * sizeof(T));
   if (e != cudaSuccess) {
     return set_err(p, e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
@@ -166,7 +175,9 @@ int check_options(const lp_options& o, std::string& msg) {
   if (o.precision != LP_PREC_FP64 && o.precision != LP_PREC_MIXED) return msg = "unknown precision", 1;
   if (o.kernel_timing < 0) return msg = "kernel_timing must be >= 0", 1;
   if (!(o.refine_tol >= 0.0)) return msg = "refine_tol must be >= 0", 1;
-  for (int i = 0; i < 8; ++i)
+  if ((o.device_alloc == nullptr) != (o.device_free == nullptr))
+    return msg = "device_alloc and device_free must be given together", 1;
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return msg = "reserved option fields must be zero", 1;
   return 0;
 }
@@ -619,7 +630,11 @@ void release(lp_problem* p) {
   for (auto e : p->events)
     if (e) cudaEventDestroy(e);
   for (void* v : p->allocs) cudaFree(v);
-  if (p->arena) cudaFree(p->arena);
+  for (const auto& a : p->ext_allocs) p->opt.device_free(a.first, a.second, p->opt.alloc_ctx);
+  if (p->arena) {
+    if (p->opt.device_alloc) p->opt.device_free(p->arena, p->arena_size, p->opt.alloc_ctx);
+    else cudaFree(p->arena);
+  }
   if (p->h_status) cudaFreeHost(p->h_status);
   if (p->h_scratch) cudaFreeHost(p->h_scratch);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -705,7 +720,15 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
     int64_t bytes = 0;
     if (lp_memory_bytes(m, n, lay.nnz, &o, &bytes) == LP_OK && bytes > 0) {
       void* a = nullptr;
-      if (cudaMalloc(&a, (size_t)bytes) == cudaSuccess) {
+      if (o.device_alloc) {
+        a = o.device_alloc((size_t)bytes, o.alloc_ctx);
+        if (!a) {
+          set_err(p, LP_ERR_OOM, "device_alloc of " + std::to_string(bytes) + " bytes returned NULL");
+          return fail(LP_ERR_OOM);
+        }
+        p->arena = static_cast<char*>(a);
+        p->arena_size = (size_t)bytes;
+      } else if (cudaMalloc(&a, (size_t)bytes) == cudaSuccess) {
         p->arena = static_cast<char*>(a);
         p->arena_size = (size_t)bytes;
       } else {

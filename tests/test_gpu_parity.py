@@ -379,6 +379,31 @@ def test_device_memory_of_a_problem_within_lp_memory_bytes(precision):
         p.close()
 
 
+def test_device_buffers_from_the_caller_allocator():
+    """With device_alloc / device_free (here PyTorch's caching allocator) a
+    problem's buffers come from the caller's pool -- one block of
+    lp_memory_bytes -- and go back to it on destroy; the solve is bitwise the
+    same as with the library's own allocation."""
+    torch = pytest.importorskip("torch")
+    lp = lpgen.transport(0, 2000, 2000, 16000)
+    o = oracle.Options(alpha=1e-4, phi=20)
+    with lpop.Problem(lp, **gpu_options(o)) as p:
+        p.solve(1e-4, 5000)
+        want = p.iterate()
+    alloc = lpop.TorchDeviceAllocator()
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    bound = lpop.lp_memory_bytes(lp.m, lp.n, lp.nnz, lpop.lp_options_default())
+    with lpop.Problem(lp, allocator=alloc, **gpu_options(o)) as p:
+        assert torch.cuda.memory_allocated() - before >= bound
+        p.solve(1e-4, 5000)
+        got = p.iterate()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == before
+    for key in ("x", "y", "T", "Sigma"):
+        assert np.array_equal(got[key], want[key]), key
+
+
 def test_alpha_zero_keeps_identity_preconditioners():
     lp = lpgen.mixed_small(4)
     o = oracle.Options(alpha=0.0, phi=1)

@@ -101,7 +101,7 @@ def test_invalid_input_is_rejected_on_the_host(lib, what):
 @pytest.mark.parametrize("field,value", [("mode", 7), ("scheduler", 5), ("alpha", -1.0), ("check_every", 0),
                                          ("check_every", (1 << 16) + 1),
                                          ("precond_floor", 0.0), ("pc_beta", 3.0), ("ruiz_iters", -1),
-                                         ("kernel_timing", -1)])
+                                         ("kernel_timing", -1), ("device_alloc", 4096), ("device_free", 4096)])
 def test_invalid_options_are_rejected(lib, field, value):
     lp = lpgen.mixed_small(0, m=12, n=20)
     opts = lpop.lp_options_default()
