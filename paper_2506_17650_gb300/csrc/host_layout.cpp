@@ -424,10 +424,10 @@ std::vector<int> segment_long_rows(BinTable& bt, const std::vector<int>& rp, int
   const int nseg_units = (int)units.size() / 2;
   BinTable out = bt;
   out.nbins = 0;
-  out.bin[out.nbins++] = Bin{blk.row_begin, r, kSegmented, 0};
+  out.bin[out.nbins++] = Bin{blk.row_begin, r, kSegmented, 0, 0, 0};
   int unit = nseg_units;
   if (r < blk.row_end) {
-    out.bin[out.nbins++] = Bin{r, blk.row_end, 0, unit};
+    out.bin[out.nbins++] = Bin{r, blk.row_end, 0, unit, 0, 0};
     unit += blk.row_end - r;
   }
   for (int b = 1; b < bt.nbins; ++b) {
