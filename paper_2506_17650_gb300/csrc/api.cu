@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -94,11 +95,20 @@ const double* step_table(int dev, cudaStream_t s, cudaError_t* err) {
   }
   if (!g_step_tab[dev]) {
     std::vector<double> h(2 * (size_t)kStepTab);
-    for (int t = 0; t < kStepTab; ++t) {
-      const double tp1 = (double)t + 1.0;
-      h[t] = 1.0 - std::pow(tp1, -0.3);
-      h[kStepTab + t] = 1.0 + std::pow(tp1, -0.6);
-    }
+    // every entry on its own, so the host threads' split does not change the table
+    auto fill = [&h](int t0, int t1) {
+      for (int t = t0; t < t1; ++t) {
+        const double tp1 = (double)t + 1.0;
+        h[t] = 1.0 - std::pow(tp1, -0.3);
+        h[kStepTab + t] = 1.0 + std::pow(tp1, -0.6);
+      }
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int T = (int)std::min<unsigned>(hw == 0 ? 1u : hw, 8u);
+    std::vector<std::thread> pool;
+    for (int i = 1; i < T; ++i) pool.emplace_back(fill, (int)((long long)kStepTab * i / T), (int)((long long)kStepTab * (i + 1) / T));
+    fill(0, (int)((long long)kStepTab / T));
+    for (auto& th : pool) th.join();
     void* dptr = nullptr;
     *err = cudaMalloc(&dptr, h.size() * sizeof(double));
     if (*err != cudaSuccess) return nullptr;
