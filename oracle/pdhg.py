@@ -398,7 +398,12 @@ def attempt(P: Scaled, S: State, opts: Options) -> bool:
     pdlp mode: the step is accepted iff eta <= eta_max (reading R8); a rejected
     attempt leaves (x, y, T, Sigma) unchanged and retries with the new eta.
     On acceptance: if k mod phi = 0 the preconditioners take one online step
-    (Algorithm 1), the eta-weighted averages are updated, and k increases."""
+    (Algorithm 1), the eta-weighted averages are updated, and k increases.
+
+    Pinned by: the hand-derived steps and the rejected attempt of
+    tests/golden/one_step_1x2.json (half-steps, gradients, eta_max).  The
+    next-step-size formula beyond eta_max (factors with exponents 0.3 and
+    0.6, a prior-art reading): parity unpinned."""
     eta, omega = S.eta, S.omega
     update_now = opts.phi > 0 and (S.k % opts.phi == 0)
     x_new, g, x_half = primal_half_step(P, S.x, S.y, S.T, eta, omega)
@@ -483,7 +488,12 @@ def _converged(kk, tol):
 def check(P: Scaled, S: State, opts: Options, tol: float, eval_only: bool = False):
     """KKT check, termination and (pdlp mode) restart decision (readings R9, R10).
 
-    ``eval_only`` only refreshes ``S.stats`` for the current iterate."""
+    ``eval_only`` only refreshes ``S.stats`` for the current iterate.
+
+    Pinned by: the KKT quantities (``kkt``, hand-computed example) and
+    convergence to the vertex / HiGHS optimum.  The restart rule itself
+    (constants 0.2, 0.8, 0.36 and the primal-weight update, prior-art
+    readings): parity unpinned."""
     aty = P.At @ S.y
     cur = kkt(P, S.x, S.y, S.ax, aty)
     if eval_only:
