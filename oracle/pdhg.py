@@ -237,7 +237,8 @@ def scale_problem(lp, opts: Options) -> Scaled:
     """Preprocess: Ruiz (``ruiz_iters`` rounds), then Pock-Chambolle (pdlp
     mode, Section 4.3 uses cuPDLP.jl defaults) or L2 rescaling (plain mode,
     Section 4.2).  Bounds, costs and right-hand side are rescaled with the
-    same diagonal factors."""
+    same diagonal factors.  Pinned by: the closed forms of its stages (below)
+    and the optimum it preserves (HiGHS on the original and the scaled LP)."""
     A = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
     A.sum_duplicates()
     A.sort_indices()
@@ -271,14 +272,16 @@ def scale_problem(lp, opts: Options) -> Scaled:
 # --------------------------------------------------------------------------
 
 def lagrangian(P: Scaled, x, y):
-    """L(x, y) = c^T x - y^T A x + b^T y (Eq. (2))."""
+    """L(x, y) = c^T x - y^T A x + b^T y (Eq. (2)).  Pinned by: L(x*, y*) =
+    c^T x* at constructed optima, and a value worked by hand."""
     return float(P.c @ x - y @ (P.A @ x) + P.b @ y)
 
 
 def initial_state(P: Scaled, opts: Options) -> State:
     """x_0 = proj_[l,u](0), y_0 = 0, T_0 = I, Sigma_0 = I (Section 3.2);
     omega_0 = ||c~|| / ||b~|| (1 if either is 0); eta_0 = 1 / max|A~_ij| in pdlp
-    mode, 0.9 / ||A~||_2 in plain mode (reading R13)."""
+    mode, 0.9 / ||A~||_2 in plain mode (reading R13).  Pinned by: special
+    cases (box positions of 0, b = 0) and the SVD norm (tests)."""
     m, n = P.A.shape
     x = np.minimum(np.maximum(np.zeros(n), P.l), P.u)
     y = np.zeros(m)
@@ -301,7 +304,8 @@ def initial_state(P: Scaled, opts: Options) -> State:
 
 def primal_half_step(P: Scaled, x, y, T, eta, omega):
     """x^{k+1} = proj_[l,u](x^k - (eta/omega) T (c - A^T y^k)) (Eq. (6), first line).
-    Returns (x^{k+1}, g = c - A^T y^k, x^{k+1/2})."""
+    Returns (x^{k+1}, g = c - A^T y^k, x^{k+1/2}).  Pinned by: the
+    hand-derived steps of tests/golden/one_step_1x2.json."""
     g = P.c - P.At @ y
     x_half = x - (eta / omega) * T * g
     x_new = np.minimum(np.maximum(x_half, P.l), P.u)
@@ -309,7 +313,8 @@ def primal_half_step(P: Scaled, x, y, T, eta, omega):
 
 
 def project_dual(P: Scaled, y_half):
-    """Projection of y onto its sign cone per row sense (reading R3)."""
+    """Projection of y onto its sign cone per row sense (reading R3).
+    Pinned by: hand values for each sense (tests)."""
     y = y_half.copy()
     g = P.sense == SENSE_G
     l = P.sense == SENSE_L
@@ -319,14 +324,16 @@ def project_dual(P: Scaled, y_half):
 
 
 def dual_feasible_mask(P: Scaled, y_half):
-    """I(y^{k+1/2} inside the sign cone of its row), inclusive at 0 (reading R3)."""
+    """I(y^{k+1/2} inside the sign cone of its row), inclusive at 0 (reading R3).
+    Pinned by: hand values for each sense (tests)."""
     return np.where(P.sense == SENSE_G, y_half >= 0.0,
                     np.where(P.sense == SENSE_L, y_half <= 0.0, True))
 
 
 def dual_half_step(P: Scaled, x_new, y, ax, Sigma, eta, omega):
     """y^{k+1} = proj(y^k + eta omega Sigma (b - A(2 x^{k+1} - x^k))) (Eq. (6), second line).
-    Returns (y^{k+1}, A x^{k+1}, r = b - A(2x^{k+1} - x^k), y^{k+1/2})."""
+    Returns (y^{k+1}, A x^{k+1}, r = b - A(2x^{k+1} - x^k), y^{k+1/2}).
+    Pinned by: the hand-derived steps of tests/golden/one_step_1x2.json."""
     ax_new = P.A @ x_new
     r = P.b - (2.0 * ax_new - ax)
     y_half = y + (eta * omega) * Sigma * r
@@ -553,7 +560,8 @@ def check(P: Scaled, S: State, opts: Options, tol: float, eval_only: bool = Fals
 
 
 def unscale(P: Scaled, S: State):
-    """User-unit primal and dual: x = dc x~, y = dr y~."""
+    """User-unit primal and dual: x = dc x~, y = dr y~.  Pinned by: the
+    unscaled optimum against HiGHS and the constructed optima (tests)."""
     return P.dc * S.x, P.dr * S.y
 
 
@@ -563,7 +571,8 @@ def solve(lp, opts: Options, tol=1e-4, iter_limit=50_000, trace=None, P=None, S=
     before the first attempt and after every ``check_every``-th attempt; at the
     iteration limit off a check boundary only the current iterate's KKT is
     re-evaluated.  ``trace(P, S)`` is called after every attempt (after that
-    attempt's check, if any).  Returns (Result, P, S)."""
+    attempt's check, if any).  Returns (Result, P, S).  Pinned by: optima from
+    vertex enumeration and HiGHS, and the generators' constructed optima."""
     if P is None:
         P = scale_problem(lp, opts)
     if S is None:

@@ -157,6 +157,45 @@ def test_kkt_zero_at_constructed_optimum():
         assert max(k2["rel_pres"], k2["rel_gap"]) > 1e-6
 
 
+def test_lagrangian_at_constructed_optimum_is_the_objective():
+    """Complementary slackness makes y*^T (b - A x*) = 0 at a primal-dual
+    optimum, so L(x*, y*) of Eq. (2) equals c^T x* -- in the scaled space as
+    in the caller's; plus one value worked by hand."""
+    for lp in (lpgen.tiny_random(3), lpgen.mixed_small(2)):
+        P = oracle.scale_problem(lp, oracle.Options())
+        x, y = lp.x_opt / P.dc, lp.y_opt / P.dr
+        assert oracle.pdhg.lagrangian(P, x, y) == pytest.approx(lp.obj_opt, rel=1e-12)
+    # A = [1 1], b = 4, c = (1, -1), x = (1, 2), y = 3: (1 - 2) - 3 * 3 + 4 * 3 = 2
+    P = _scaled_from_dense([[1.0, 1.0]], [4.0], [1.0, -1.0], [0.0, 0.0], [10.0, 10.0], "E")
+    assert oracle.pdhg.lagrangian(P, arr([1.0, 2.0]), arr([3.0])) == 2.0
+
+
+def test_initial_state_special_cases():
+    """x_0 is the point of the box nearest 0, y_0 = 0, T_0 = Sigma_0 = I
+    (Section 3.2); eta_0 ||A~||_2 = 0.9 in plain mode with the norm from an
+    SVD; hand values of eta_0 and omega_0 in pdlp mode; omega_0 = 1 for b = 0."""
+    A = [[3.0, 4.0, 0.0], [0.0, 0.0, 1.0]]  # singular values 5 and 1; largest |a_ij| 4
+    P = _scaled_from_dense(A, [1.0, 2.0], [1.0, 1.0, 1.0], [-1.0, 2.0, -np.inf], [1.0, 5.0, -3.0], "EE")
+    S = oracle.initial_state(P, oracle.Options(mode="plain"))
+    np.testing.assert_array_equal(S.x, [0.0, 2.0, -3.0])
+    assert np.all(S.y == 0) and np.all(S.T == 1) and np.all(S.Sigma == 1)
+    assert S.eta * np.linalg.svd(np.array(A), compute_uv=False)[0] == pytest.approx(0.9, rel=1e-12)
+    Sp = oracle.initial_state(P, oracle.Options(mode="pdlp"))
+    assert Sp.eta == 0.25 and Sp.omega == pytest.approx(math.sqrt(3.0 / 5.0), rel=1e-15)
+    P0 = _scaled_from_dense(A, [0.0, 0.0], [1.0, 1.0, 1.0], [0.0] * 3, [1.0] * 3, "EE")
+    assert oracle.initial_state(P0, oracle.Options(mode="pdlp")).omega == 1.0
+
+
+def test_dual_projection_and_mask_per_sense():
+    """Sign cone per row sense (reading R3): equality rows free, >= rows
+    y >= 0, <= rows y <= 0; the mask is membership, inclusive at 0."""
+    P = _scaled_from_dense(np.ones((9, 1)), [0.0] * 9, [0.0], [0.0], [1.0], "EEEGGGLLL")
+    yh = arr([-2.0, 0.0, 3.0] * 3)
+    np.testing.assert_array_equal(oracle.pdhg.project_dual(P, yh), [-2, 0, 3, 0, 0, 3, -2, 0, 0])
+    np.testing.assert_array_equal(oracle.pdhg.dual_feasible_mask(P, yh),
+                                  [True, True, True, False, True, True, True, True, False])
+
+
 # ---------------------------------------------------------------------------
 # Online gradients: finite differences of the losses of Eq. (5)
 # ---------------------------------------------------------------------------
