@@ -497,10 +497,12 @@ def check(P: Scaled, S: State, opts: Options, tol: float, eval_only: bool = Fals
 
     ``eval_only`` only refreshes ``S.stats`` for the current iterate.
 
-    Pinned by: the KKT quantities (``kkt``, hand-computed example) and
-    convergence to the vertex / HiGHS optimum.  The restart rule itself
-    (constants 0.2, 0.8, 0.36 and the primal-weight update, prior-art
-    readings): parity unpinned."""
+    Pinned by: the KKT quantities (``kkt``, hand-computed example),
+    convergence to the vertex / HiGHS optimum, and restart decisions worked by
+    hand on a 1x1 LP for each condition of the restart reading (sufficient
+    decay, decay without progress, long period, candidate choice, primal
+    weight).  The reading itself (PDLP prior art, constants 0.2 / 0.8 /
+    0.36) is not fixed by the paper."""
     aty = P.At @ S.y
     cur = kkt(P, S.x, S.y, S.ax, aty)
     if eval_only:

@@ -197,6 +197,73 @@ def test_dual_projection_and_mask_per_sense():
 
 
 # ---------------------------------------------------------------------------
+# Restart decisions worked by hand (the restart reading: KKT-based restarts
+# with sufficient decay 0.2, necessary decay 0.8 without progress, and an
+# artificial restart once the period holds 0.36 of all attempts)
+# ---------------------------------------------------------------------------
+# LP: min x  s.t.  x = 1, x >= 0 (no scaling).  At (x, y) = (2, 0.5): primal
+# residual 1, reduced cost 0.5 absorbed by the bound (dual residual 0),
+# pobj 2, dobj 0.5, gap 1.5, so K_1 = sqrt(1 + 2.25) = sqrt(3.25).  At the
+# average (1.5, 0.75): residual 0.5, gap 0.75, K_1 = sqrt(0.8125).
+
+def _restart_state(x_last=(0.0,), k_last_parts=(36.0, 0.0, 144.0), k_prev=100.0, last=90, with_avg=False):
+    S = State(x=arr([2.0]), y=arr([0.5]), ax=arr([2.0]), T=np.ones(1), Sigma=np.ones(1), GT=np.zeros(1),
+              GS=np.zeros(1), GT_norm=0.0, GS_norm=0.0, eta=0.5, omega=1.0, attempts=100,
+              xbar=arr([1.5]) if with_avg else np.zeros(1), ybar=arr([0.75]) if with_avg else np.zeros(1),
+              wsum=1.0 if with_avg else 0.0)
+    S.x_last = None if x_last is None else arr(list(x_last))
+    S.y_last = None if x_last is None else np.zeros(1)
+    S.K_last_parts, S.K_prev, S.last_restart_attempt = k_last_parts, k_prev, last
+    return S
+
+
+_P1 = _scaled_from_dense([[1.0]], [1.0], [1.0], [0.0], [np.inf], "E")
+
+
+@pytest.mark.parametrize("case,parts,k_prev,last,restart", [
+    ("sufficient decay", (36.0, 0.0, 144.0), 100.0, 90, True),   # K / K_last = sqrt(3.25 / 180) < 0.2
+    ("decay without progress", (4.0, 0.0, 4.0), 1.0, 90, True),  # ratio sqrt(3.25 / 8) ~ 0.64 <= 0.8, K > K_prev
+    ("decay with progress", (4.0, 0.0, 4.0), 5.0, 90, False),    # same ratio, K < K_prev
+    ("long period", (1.0, 0.0, 2.25), 1.0, 60, True),            # ratio 1, 40 of 100 attempts >= 0.36
+    ("short period", (1.0, 0.0, 2.25), 1.0, 70, False),          # ratio 1, 30 of 100 attempts
+])
+def test_restart_decisions_by_hand(case, parts, k_prev, last, restart):
+    S = _restart_state(k_last_parts=parts, k_prev=k_prev, last=last)
+    oracle.pdhg.check(_P1, S, oracle.Options(mode="pdlp"), tol=1e-9)
+    assert S.status is None
+    assert S.restarts == (1 if restart else 0), case
+    assert S.K_prev == pytest.approx(math.sqrt(3.25), rel=1e-15)
+    if restart:
+        # restart point (2, 0.5) from (0, 0): omega <- sqrt(omega ||dy|| / ||dx||) = sqrt(0.5 / 2)
+        np.testing.assert_array_equal(S.x_last, [2.0])
+        assert S.omega == pytest.approx(0.5, rel=1e-15)
+        assert S.last_restart_attempt == 100 and S.wsum == 0.0
+        assert S.K_last_parts == pytest.approx((1.0, 0.0, 2.25), rel=1e-15)
+    else:
+        assert S.omega == 1.0 and S.last_restart_attempt == last
+
+
+def test_restart_to_the_better_average_by_hand():
+    S = _restart_state(with_avg=True)
+    oracle.pdhg.check(_P1, S, oracle.Options(mode="pdlp"), tol=1e-9)
+    assert S.restarts == 1
+    np.testing.assert_array_equal(S.x, [1.5])
+    np.testing.assert_array_equal(S.y, [0.75])
+    assert S.K_prev == pytest.approx(math.sqrt(0.8125), rel=1e-15)
+    assert S.omega == pytest.approx(math.sqrt(0.5), rel=1e-15)  # ||dy|| / ||dx|| = 0.75 / 1.5
+
+
+def test_first_check_records_the_reference_and_restarts_can_be_off():
+    S = _restart_state(x_last=None)
+    oracle.pdhg.check(_P1, S, oracle.Options(mode="pdlp"), tol=1e-9)
+    assert S.restarts == 0 and S.last_restart_attempt == 100
+    np.testing.assert_array_equal(S.x_last, [2.0])
+    S = _restart_state()
+    oracle.pdhg.check(_P1, S, oracle.Options(mode="pdlp", restart=False), tol=1e-9)
+    assert S.restarts == 0
+
+
+# ---------------------------------------------------------------------------
 # Online gradients: finite differences of the losses of Eq. (5)
 # ---------------------------------------------------------------------------
 
