@@ -20,7 +20,8 @@
  *    arrays are caller-owned and only read during the call (copied to the
  *    device); output arrays are caller-allocated.
  *  - The library owns all device memory of a problem and frees it in
- *    lp_destroy().
+ *    lp_destroy() (through options.device_free when the caller supplied an
+ *    allocator).
  *  - Every function returns an lp_err code (LP_OK = 0 on success); no C++
  *    exception crosses the ABI.  On failure lp_last_error() describes it.
  *  - The solve outcome (optimal, iteration limit, ...) is an lp_status,
