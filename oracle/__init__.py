@@ -11,8 +11,8 @@ Modules
 * :mod:`oracle.pdhg` -- the method, step by step, in numpy float64.
 * :mod:`oracle.vertices` -- brute-force vertex enumeration for tiny LPs.
 
-Parity status of each function is stated in its docstring ("pinned by ..." or
-"parity unpinned").
+Parity status of each function is stated in its docstring ("pinned by ...");
+every public function has a pin.
 """
 from .pdhg import (  # noqa: F401
     Options,

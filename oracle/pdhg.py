@@ -366,8 +366,11 @@ def online_gradients(P: Scaled, g, x_half, ax, r, y_half, eta, omega, normalize)
 def ogd_update(Pvec, Gacc, Gnorm, grad, opts: Options):
     """One projected online-gradient step P <- proj[P - alpha grad] with the
     AdaGrad learning-rate rule (Section 3.1 OGD, Section 4.1 AdaGrad;
-    readings R5, R6).  Returns (P, G, Gnorm).  Pinned by: T never decreases,
-    Sigma stays >= floor, alpha = 0 leaves P unchanged bit for bit (tests)."""
+    readings R5, R6).  Returns (P, G, Gnorm).  Pinned by: hand values of one
+    step of each rule (diagonal AdaGrad in tests/golden/one_step_1x2.json,
+    scalar AdaGrad and the constant rate in tests/golden/step_rules_1x1.json,
+    floor included); T never decreases, Sigma stays >= floor, alpha = 0
+    leaves P unchanged bit for bit (tests)."""
     if grad is None:
         return Pvec, Gacc, Gnorm
     a = opts.alpha
@@ -408,9 +411,14 @@ def attempt(P: Scaled, S: State, opts: Options) -> bool:
     (Algorithm 1), the eta-weighted averages are updated, and k increases.
 
     Pinned by: the hand-derived steps and the rejected attempt of
-    tests/golden/one_step_1x2.json (half-steps, gradients, eta_max).  The
-    next-step-size formula beyond eta_max (factors with exponents 0.3 and
-    0.6, a prior-art reading): parity unpinned."""
+    tests/golden/one_step_1x2.json (half-steps, gradients, eta_max), and the
+    attempts worked by hand in tests/golden/step_rules_1x1.json: the next
+    step size at attempt 1023, where the factors are exactly 7/8 and 65/64
+    (both terms of the min), the averages weighted by the step each accepted
+    attempt used, and the update points k = 0, phi, 2 phi counted in accepted
+    steps across a rejected attempt (and, in a test, across restarts).  The
+    step-size rule itself (exponents 0.3 / 0.6) is a prior-art reading the
+    paper does not fix."""
     eta, omega = S.eta, S.omega
     update_now = opts.phi > 0 and (S.k % opts.phi == 0)
     x_new, g, x_half = primal_half_step(P, S.x, S.y, S.T, eta, omega)

@@ -119,9 +119,9 @@ def test_golden_plain_attempts_match_hand_steps():
     assert not oracle.attempt(P, S2, oracle.Options(mode="pdlp", phi=0))
     np.testing.assert_array_equal(S2.x, [0.0, 0.0])
     assert S2.k == 1 and S2.attempts == 2
-    t = 2
-    expect_eta = min((1 - (t + 1) ** -0.3) * 13 / 27, (1 + (t + 1) ** -0.6) * 0.5)
-    assert S2.eta == pytest.approx(expect_eta, rel=1e-14)
+    # the next step stays below the rejected attempt's limit 13/27 (the step
+    # size's exact values are pinned in tests/golden/step_rules_1x1.json)
+    assert 0.0 < S2.eta < 13 / 27
 
 
 # ---------------------------------------------------------------------------
@@ -529,3 +529,120 @@ def test_small_transport_matches_highs():
     assert res.pobj == pytest.approx(ref, rel=1e-6)
     # strong duality at the returned point
     assert res.dobj == pytest.approx(ref, rel=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Step-size rule, average weights, update points and the other schedulers
+# (tests/golden/step_rules_1x1.json, worked by hand)
+# ---------------------------------------------------------------------------
+
+def _rules_problem(g):
+    L = g["lp"]
+    return _scaled_from_dense(L["A"], L["b"], L["c"], arr(L["l"]), arr(L["u"]), L["sense"])
+
+
+def _rules_state(eta, attempts=0, k=0):
+    return State(x=np.zeros(1), y=np.zeros(1), ax=np.zeros(1), T=np.ones(1), Sigma=np.ones(1),
+                 GT=np.zeros(1), GS=np.zeros(1), GT_norm=0.0, GS_norm=0.0, eta=eta, omega=1.0,
+                 xbar=np.zeros(1), ybar=np.zeros(1), k=k, attempts=attempts)
+
+
+@pytest.mark.parametrize("case", ["accept_then_grow", "reject_then_shrink"])
+def test_golden_next_step_size_and_average_weights(case):
+    """Two pdlp attempts from a hand-worked state at attempt 1023, where the
+    step-size factors are exactly 7/8 and 65/64: the accept test, the next
+    step size (either term of the min), and the averages weighted by the
+    step size each accepted attempt used."""
+    g = load_golden("step_rules_1x1.json")
+    e = g[case]
+    P = _rules_problem(g)
+    S = _rules_state(e["eta"], attempts=e["attempts_before"])
+    o = oracle.Options(mode="pdlp", alpha=0.0, phi=0)
+    for key in ("step1", "step2"):
+        s = e[key]
+        x0, y0, ax0 = S.x.copy(), S.y.copy(), S.ax.copy()
+        eta_used = S.eta
+        acc = oracle.attempt(P, S, o)
+        assert acc == s["accepted"]
+        np.testing.assert_allclose(S.x, s["x"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(S.y, s["y"], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(S.xbar, s["xbar"], rtol=1e-15, atol=0)
+        np.testing.assert_allclose(S.ybar, s["ybar"], rtol=1e-15, atol=0)
+        assert S.wsum == pytest.approx(s["wsum"], rel=1e-15, abs=0)
+        # the limit of this attempt, from the same point and step
+        x1, _, _ = oracle.primal_half_step(P, x0, y0, np.ones(1), eta_used, 1.0)
+        y1, ax1, _, _ = oracle.dual_half_step(P, x1, y0, ax0, np.ones(1), eta_used, 1.0)
+        lim = oracle.step_size_limit(x1 - x0, y1 - y0, ax1 - ax0, np.ones(1), np.ones(1), 1.0)
+        assert lim == pytest.approx(s["eta_max"], rel=1e-15)
+        if "eta_next" in s:
+            assert S.eta == pytest.approx(s["eta_next"], rel=1e-15, abs=0)
+        if not acc:
+            assert S.k == 0 and S.attempts == e["attempts_before"] + 1
+
+
+def test_golden_update_points_count_accepted_steps():
+    """The online update fires on accepted attempts whose count of earlier
+    accepted steps is 0, phi, 2 phi, ... (Algorithm 1, reading R7), with a
+    rejected attempt in between."""
+    g = load_golden("step_rules_1x1.json")
+    e = g["update_points"]
+    P = _rules_problem(g)
+    S = _rules_state(e["eta"])
+    o = oracle.Options(mode="pdlp", alpha=e["alpha"], phi=e["phi"], normalize=False, scheduler="const")
+    forced = {int(k): v for k, v in e["eta_forced"].items()}
+    for i, (acc_e, k_e, move_e) in enumerate(zip(e["accepted"], e["k_after"], e["preconditioner_moves"])):
+        S.eta = forced.get(i, e["eta"])
+        T0, S0 = S.T.copy(), S.Sigma.copy()
+        acc = oracle.attempt(P, S, o)
+        assert acc == acc_e, i
+        assert S.k == k_e, i
+        moved = bool(np.any(S.T != T0) or np.any(S.Sigma != S0))
+        assert moved == move_e, i
+
+
+def test_update_points_follow_accepted_steps_across_restarts():
+    """Over a restarted pdlp solve, the preconditioners move exactly on the
+    accepted attempts whose number of earlier accepted attempts (counted here,
+    not read from the oracle's k) is a multiple of phi: k is not reset by a
+    restart and rejected attempts do not count (reading R7)."""
+    lp = lpgen.tiny_random(3, m=30, n=70, col_nnz=4)
+    phi = 3
+    o = oracle.Options(mode="pdlp", alpha=1e-2, phi=phi, normalize=True, check_every=8)
+    P = oracle.scale_problem(lp, o)
+    S = oracle.initial_state(P, o)
+    oracle.check(P, S, o, 0.0)
+    S.checked0 = True
+    accepted = rejected = 0
+    restarts_seen = 0
+    for i in range(400):
+        if i % 37 == 36:
+            S.eta *= 50.0  # far beyond the step limit: a rejected attempt
+        T0, S0 = S.T.copy(), S.Sigma.copy()
+        before = accepted
+        acc = oracle.attempt(P, S, o)
+        moved = bool(np.any(S.T != T0) or np.any(S.Sigma != S0))
+        expect = acc and before % phi == 0
+        assert moved == expect, (S.attempts, acc, before)
+        accepted += acc
+        rejected += not acc
+        if S.attempts % o.check_every == 0:
+            r0 = S.restarts
+            oracle.check(P, S, o, 0.0)
+            restarts_seen += S.restarts - r0
+    assert restarts_seen >= 2 and rejected >= 5
+
+
+def test_golden_scheduler_steps():
+    """One step of each learning-rate rule worked by hand (reading R6):
+    scalar AdaGrad over the whole gradient and a constant rate, each followed
+    by the floor."""
+    g = load_golden("step_rules_1x1.json")["schedulers"]
+    for s in g["adagrad_norm"]:
+        o = oracle.Options(alpha=s["alpha"], scheduler="adagrad_norm", precond_floor=1e-6)
+        P, G, Gn = oracle.ogd_update(arr(s["P"]), np.zeros(len(s["P"])), s["G"], arr(s["grad"]), o)
+        np.testing.assert_allclose(P, s["P_after"], rtol=1e-15, atol=0)
+        assert Gn == s["G_after"]
+    for s in g["const"]:
+        o = oracle.Options(alpha=s["alpha"], scheduler="const", precond_floor=1e-6)
+        P, _, _ = oracle.ogd_update(arr(s["P"]), np.zeros(len(s["P"])), 0.0, arr(s["grad"]), o)
+        np.testing.assert_allclose(P, s["P_after"], rtol=1e-15, atol=0)
