@@ -83,8 +83,10 @@ enum {
 /* Optional allocator for a problem's device buffers, for callers whose device
  * memory belongs to a framework (for example a caching allocator).  alloc
  * returns at least `bytes` bytes of device memory on the problem's device,
- * aligned to 256 bytes, or NULL (lp_create then fails with LP_ERR_OOM); free
- * returns a block alloc gave, with the same size.  Both are called only from
+ * aligned to 256 bytes, or NULL (lp_create then fails with LP_ERR_OOM); a
+ * block that is not 256-byte aligned is handed straight back to free and
+ * lp_create fails with LP_ERR_INVALID_ARG.  free returns a block alloc gave,
+ * with the same size.  Both are called only from
  * lp_create and lp_destroy, on the calling thread; lp_destroy synchronises the
  * problem's stream before it frees. */
 typedef void* (*lp_device_alloc_fn)(size_t bytes, void* ctx);
@@ -262,7 +264,9 @@ int lp_kernel_times(lp_problem* p, double* ms, int64_t* samples, int32_t n_kerne
  *   norm_out    HOST pointer receiving sqrt(||A^T A v||) of the last round
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the one array and leave their data in it;
+ * stream capture.  The cached address does not survive cudaDeviceReset (the
+ * module and its array may then move): do not call this entry point again in
+ * a process after resetting the device.  All calls share the one array and leave their data in it;
  * nothing in it needs to start at zero.  Calls whose work overlaps on the GPU
  * (other threads or streams) race on the array: serialise them.
  * Errors: LP_ERR_INVALID_ARG (sizes, NULL pointers), LP_ERR_CUDA; the message
@@ -283,8 +287,10 @@ int lp_power_norm_noalloc(int32_t m, int32_t n, const int32_t* a_row_ptr, const 
  * by a thread-block cluster of cluster_size CTAs, the others by one CTA each;
  * members are assigned longest-first by nonzero count.  After each round the
  * members' host views are refreshed, so lp_result / lp_get_state work on them
- * as after lp_solve.  All members must live on one device; the batch uses the
- * first member's stream.  Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
+ * as after lp_solve.  All members must live on one device.  The batch runs on
+ * its own stream, created on the members' device; each member's pending work
+ * on its own stream has finished before the batch first reads that member.
+ * Errors: LP_ERR_INVALID_ARG, LP_ERR_CUDA.
  */
 typedef struct lp_batch lp_batch;
 

@@ -67,9 +67,25 @@ class LP:
         return sp.csr_matrix((self.val, self.col_idx, self.row_ptr), shape=(self.m, self.n))
 
 
+def _sorted_unique(a):
+    """np.unique(a) for an integer array, by one sort and a neighbour test (the
+    hash-based path of np.unique is many times slower on tens of millions of keys)."""
+    a = np.sort(a)
+    if a.size > 1:
+        keep = np.empty(a.size, dtype=bool)
+        keep[0] = True
+        np.not_equal(a[1:], a[:-1], out=keep[1:])
+        a = a[keep]
+    return a
+
+
 def _csr_from_coo(m, n, rows, cols, vals):
     """Sorted, duplicate-free CSR arrays from coordinate triplets (no summing: callers pass distinct pairs)."""
-    order = np.lexsort((cols, rows))
+    key = np.asarray(rows, dtype=np.int64) * max(int(n), 1) + np.asarray(cols, dtype=np.int64)
+    order = np.argsort(key)  # keys are distinct, so this is the (row, col) order
+    ks = key[order]
+    if ks.size > 1 and np.any(ks[1:] == ks[:-1]):
+        raise ValueError("repeated (row, column) pair")
     rows = rows[order]
     cols = cols[order]
     vals = vals[order]
@@ -89,7 +105,7 @@ def _distinct_rows_per_column(rng, m, degrees):
     degrees = np.asarray(degrees, dtype=np.int64)
     cols = np.repeat(np.arange(degrees.size, dtype=np.int64), degrees)
     rows = rng.integers(0, m, size=cols.size, dtype=np.int64)
-    key = np.unique(cols * m + rows)
+    key = _sorted_unique(cols * m + rows)
     return (key % m), (key // m)
 
 
@@ -344,7 +360,7 @@ def long_rows(seed=0, m=9000, n=12000, row_lengths=(4097, 8192, 11000), col_leng
         keys.append(rng.choice(n, size=L, replace=False) * m + r)
     for c, L in zip(long_c, col_lengths):
         keys.append(c * m + rng.choice(m, size=L, replace=False))
-    key = np.unique(np.concatenate(keys))
+    key = _sorted_unique(np.concatenate(keys))
     rows, cols = key % m, key // m
     # the long rows / columns hold exactly their lengths, except for entries
     # shared with another long line or the background; trim those from the background

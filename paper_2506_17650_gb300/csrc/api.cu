@@ -151,6 +151,10 @@ int dalloc(lp_problem* p, T** ptr, size_t count) {
   if (p->opt.device_alloc) {
     v = p->opt.device_alloc(bytes, p->opt.alloc_ctx);
     if (!v) return set_err(p, LP_ERR_OOM, "device_alloc of " + std::to_string(bytes) + " bytes returned NULL");
+    if (reinterpret_cast<uintptr_t>(v) & 255u) {  // the kernels' vector loads need the 256-byte alignment
+      p->opt.device_free(v, bytes, p->opt.alloc_ctx);
+      return set_err(p, LP_ERR_INVALID_ARG, "device_alloc returned an address that is not 256-byte aligned");
+    }
     p->ext_allocs.emplace_back(v, bytes);
     *ptr = static_cast<T*>(v);
     return LP_OK;
@@ -735,6 +739,11 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
         if (!a) {
           set_err(p, LP_ERR_OOM, "device_alloc of " + std::to_string(bytes) + " bytes returned NULL");
           return fail(LP_ERR_OOM);
+        }
+        if (reinterpret_cast<uintptr_t>(a) & 255u) {  // buffers are carved from it in 256-byte steps
+          o.device_free(a, (size_t)bytes, o.alloc_ctx);
+          set_err(p, LP_ERR_INVALID_ARG, "device_alloc returned an address that is not 256-byte aligned");
+          return fail(LP_ERR_INVALID_ARG);
         }
         p->arena = static_cast<char*>(a);
         p->arena_size = (size_t)bytes;

@@ -42,7 +42,7 @@ def mixed(o, **extra):
 
 
 @pytest.mark.parametrize("case", ["tiny_plain_norm_freq", "tiny_pdlp_freq", "mixed_pdlp_adagrad", "rowmix_pdlp",
-                                  "transport_small_pdlp"])
+                                  "transport_small_pdlp", "powerlaw_small_pdlp"])
 def test_mixed_one_step_from_oracle_state(case):
     make, o = CASES[case]
     lp = make()
@@ -60,7 +60,7 @@ def test_mixed_one_step_from_oracle_state(case):
 
 
 @pytest.mark.parametrize("case", ["tiny_plain_norm_freq", "tiny_pdlp_freq", "mixed_pdlp_adagrad", "rowmix_pdlp",
-                                  "transport_small_pdlp"])
+                                  "transport_small_pdlp", "powerlaw_tiny_pdlp"])
 def test_mixed_solve_to_1e4_is_certified(case):
     make, o = CASES[case]
     lp = make()

@@ -107,6 +107,12 @@ CASES = {
     "alpha0_pdlp": (lambda: lpgen.mixed_small(3), oracle.Options(alpha=0.0, phi=1)),
     # rows of A and of A^T longer than a segment (4096 entries here): reduced by several blocks
     "long_rows_pdlp": (lambda: lpgen.long_rows(0), oracle.Options(alpha=1e-3, phi=1)),
+    # the large power-law LP's recipe at 1% of its size (m 20k, n 50k, ~300k nonzeros): column
+    # degrees up to 20k (segmented rows of A^T), |a| over six decades, free and boxed variables,
+    # = and <= rows; the bench's online-preconditioning settings
+    "powerlaw_small_pdlp": (lambda: lpgen.powerlaw(0, 20_000, 50_000, 300_000), oracle.Options(alpha=1e-6, phi=20)),
+    # the same recipe at 0.05% (m 1000, n 2500, ~13k nonzeros): small enough to solve to 1e-4
+    "powerlaw_tiny_pdlp": (lambda: lpgen.powerlaw(0, 1_000, 2_500, 15_000), oracle.Options(alpha=1e-6, phi=20)),
 }
 
 
@@ -250,7 +256,7 @@ def oracle_count_range(lp, o, tol, seeds=5, iter_limit=100_000):
 
 
 @pytest.mark.parametrize("case", ["tiny_plain_norm_freq", "tiny_pdlp_freq", "mixed_pdlp_adagrad",
-                                  "rowmix_pdlp", "transport_small_pdlp"])
+                                  "rowmix_pdlp", "transport_small_pdlp", "powerlaw_tiny_pdlp"])
 def test_full_solve_matches_oracle(case):
     make, o = CASES[case]
     lp = make()
