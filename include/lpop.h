@@ -329,9 +329,14 @@ int lp_batch_set_handoff(lp_batch* b, int64_t attempts);
 
 /* Schedule autotuner: for cluster sizes {1, 2, 4, 8} and wide thresholds at
  * the 50/80/95/99th percentiles of the members' nonzero counts, reset every
- * member (lp_reset), time one round of trial_attempts attempts with CUDA
- * events, keep the fastest schedule, and reset the members again.  Outputs
- * (may be NULL): the chosen cluster size and threshold, its trial time. */
+ * member (lp_reset) and time a whole lp_batch_solve to rel_kkt_tol with an
+ * attempt limit of trial_attempts per member, rounds of 256 attempts and the
+ * batch's handoff (host clock: handed-off members run on their own streams),
+ * so that the trial sees the slowest members, the tail the schedule must
+ * hide; keep the fastest schedule and reset the members again.  A trial
+ * limit at least as large as the real solve's measures exactly what that
+ * solve will take.  Outputs (may be NULL): the chosen cluster size and
+ * threshold, its trial time in ms. */
 int lp_batch_autotune(lp_batch* b, double rel_kkt_tol, int32_t trial_attempts, int32_t* cluster_size,
                       int64_t* wide_nnz, double* trial_ms);
 

@@ -34,6 +34,9 @@ Readings of points the paper leaves open (each is a decision, not a quote):
 * R8 adaptive step (PDLP prior art): eta_max = (omega ||dx||^2_{T^-1} +
   ||dy||^2_{Sigma^-1} / omega) / (2 |dy^T A dx|); accept iff eta <= eta_max;
   next eta = min((1 - (t+1)^-0.3) eta_max, (1 + (t+1)^-0.6) eta), t = attempts so far.
+  An interaction of exactly 0 gives eta_max = inf; a non-finite step that
+  makes eta_max NaN rejects the attempt, and the next eta is then the growth
+  term (1 + (t+1)^-0.6) eta alone.
 * R9 restarts (PDLP prior art): every ``check_every`` attempts, candidate =
   current or eta-weighted average, whichever has the smaller weighted KKT
   K_w = sqrt(w^2 ||pres||^2 + ||dres||^2 / w^2 + gap^2) (scaled space);
@@ -428,7 +431,10 @@ def attempt(P: Scaled, S: State, opts: Options) -> bool:
         eta_max = step_size_limit(x_new - S.x, y_new - S.y, ax_new - S.ax, S.T, S.Sigma, omega)
         accept = eta <= eta_max
         t = S.attempts
-        eta_next = min((1.0 - (t + 1) ** -0.3) * eta_max, (1.0 + (t + 1) ** -0.6) * eta)
+        if math.isnan(eta_max):  # no limit could be formed (non-finite step): grow from eta
+            eta_next = (1.0 + (t + 1) ** -0.6) * eta
+        else:
+            eta_next = min((1.0 - (t + 1) ** -0.3) * eta_max, (1.0 + (t + 1) ** -0.6) * eta)
     else:
         accept = True
         eta_next = eta

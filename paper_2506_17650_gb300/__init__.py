@@ -454,7 +454,8 @@ def lp_batch_solve(batch, rel_kkt_tol=1e-4, iter_limit=1_000_000, round_attempts
 
 
 def lp_batch_autotune(batch, rel_kkt_tol=1e-4, trial_attempts=128):
-    """Pick the fastest team schedule on a trial round (resets every member); returns (cluster, wide_nnz, ms)."""
+    """Pick the fastest team schedule on whole trial solves (attempt limit trial_attempts, the batch's
+    handoff); resets every member before and after.  Returns (cluster, wide_nnz, ms)."""
     c = c_int32(0)
     w = c_int64(0)
     ms = c_double(0.0)

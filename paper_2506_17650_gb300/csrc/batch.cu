@@ -754,6 +754,9 @@ int lp_batch_set_handoff(lp_batch* b, int64_t attempts) {
   return LP_OK;
 }
 
+// rounds of the autotuner's trial solves (the binding's default for lp_batch_solve)
+constexpr int32_t kTuneRound = 256;
+
 int lp_batch_autotune(lp_batch* b, double rel_kkt_tol, int32_t trial_attempts, int32_t* cluster_size,
                       int64_t* wide_nnz, double* trial_ms) {
   if (!b) return berr(nullptr, LP_ERR_INVALID_ARG, "batch handle is NULL");
@@ -766,10 +769,7 @@ int lp_batch_autotune(lp_batch* b, double rel_kkt_tol, int32_t trial_attempts, i
   std::sort(sorted.begin(), sorted.end());
   std::vector<long long> thresholds = {1LL << 62};
   for (double q : {0.5, 0.8, 0.95, 0.99}) thresholds.push_back(sorted[(size_t)(q * (count - 1))]);
-  cudaEvent_t e0, e1;
-  BCK(cudaEventCreate(&e0));
-  BCK(cudaEventCreate(&e1));
-  float best = 1e30f;
+  double best = 1e300;
   int best_c = 1;
   long long best_w = 1LL << 62;
   for (int C : {1, 2, 4, 8}) {
@@ -784,16 +784,14 @@ int lp_batch_autotune(lp_batch* b, double rel_kkt_tol, int32_t trial_attempts, i
       if (rc != LP_OK) return rc;
       b->cluster = C;
       b->wide_nnz = w;
-      BCK(cudaEventRecord(e0, b->stream));
-      rc = lp_batch_round(b, rel_kkt_tol, trial_attempts, 1LL << 62, nullptr);
+      BCK(cudaStreamSynchronize(b->stream));
+      const auto t0 = std::chrono::steady_clock::now();
+      rc = lp_batch_solve(b, rel_kkt_tol, trial_attempts, kTuneRound, nullptr);
       if (rc != LP_OK) {
         if (C > 1) continue;  // a cluster size the device cannot launch is skipped
         return rc;
       }
-      BCK(cudaEventRecord(e1, b->stream));
-      BCK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      BCK(cudaEventElapsedTime(&ms, e0, e1));
+      const double ms = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       if (ms < best) {
         best = ms;
         best_c = C;
@@ -801,8 +799,6 @@ int lp_batch_autotune(lp_batch* b, double rel_kkt_tol, int32_t trial_attempts, i
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   for (lp_problem* p : b->probs) {
     const int rc = lp_reset(p);
     if (rc != LP_OK) return berr(b, rc, "reset of a member failed");

@@ -210,9 +210,10 @@ __device__ inline void step_control_t(DevState& s, const Params& prm, double f1,
   if (Pdlp) {
     const double movement = omega * t1[0] + t2[0] * inv_omega;
     const double interaction = fabs(t2[1]);
-    // interaction > 0 (NaN excluded)
+    // no interaction (exactly 0): every step passes; a NaN interaction gives a
+    // NaN limit, which rejects the attempt
     const long long ib = __double_as_longlong(interaction);
-    const double eta_max = (ib > 0 && ib <= 0x7ff0000000000000LL) ? movement / (2.0 * interaction) : INFINITY;
+    const double eta_max = ib == 0 ? INFINITY : movement / (2.0 * interaction);
     // eta <= eta_max (both >= 0; false for NaN)
     const long long mb = __double_as_longlong(eta_max);
     accept = !nan_bits(mb) && __double_as_longlong(eta) <= mb;

@@ -177,9 +177,19 @@ class Server:
         self.batch.close()
 
     def latency_report(self):
-        t = np.array([r.time_to_tol for r in self.done.values() if r.time_to_tol is not None])
-        ok = sum(1 for r in self.done.values() if r.status == LP_OPTIMAL)
-        if t.size == 0:
+        """Time to tolerance (finish - arrival) over the requests that reached
+        the tolerance, with their count; requests that stopped at the attempt
+        limit (or failed) are reported apart, with their time to that stop."""
+        done = [r for r in self.done.values() if r.time_to_tol is not None]
+        if not done:
             return {"finished": 0}
-        return {"finished": int(t.size), "optimal": ok, "p50_s": float(np.percentile(t, 50)),
-                "p99_s": float(np.percentile(t, 99)), "mean_s": float(t.mean()), "rounds": self.rounds}
+        solved = np.array([r.time_to_tol for r in done if r.status == LP_OPTIMAL])
+        capped = np.array([r.time_to_tol for r in done if r.status != LP_OPTIMAL])
+        out = {"finished": len(done), "reached_tol": int(solved.size), "stopped_before_tol": int(capped.size),
+               "rounds": self.rounds}
+        if solved.size:
+            out.update(p50_s=float(np.percentile(solved, 50)), p99_s=float(np.percentile(solved, 99)),
+                       mean_s=float(solved.mean()))
+        if capped.size:
+            out.update(stopped_p50_s=float(np.percentile(capped, 50)), stopped_p99_s=float(np.percentile(capped, 99)))
+        return out

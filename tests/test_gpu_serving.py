@@ -63,7 +63,7 @@ def test_stream_is_solved_and_certified():
             assert req.status == lpop.LP_OPTIMAL, lp.name
             assert _certified(lp, req) <= 1.01e-4, lp.name
         rep = srv.latency_report()
-        assert rep["finished"] == len(lps) and rep["optimal"] == len(lps)
+        assert rep["finished"] == len(lps) and rep["reached_tol"] == len(lps)
     finally:
         srv.close()
 

@@ -176,6 +176,23 @@ def test_latency_report(fake):
     srv.drain()
     rep = srv.latency_report()
     times = sorted(r.time_to_tol for r in srv.done.values())
-    assert rep["finished"] == 3 and rep["optimal"] == 3 and rep["rounds"] == 3
+    assert rep["finished"] == 3 and rep["reached_tol"] == 3 and rep["rounds"] == 3
+    assert rep["stopped_before_tol"] == 0 and "stopped_p50_s" not in rep
     assert times[0] < times[1] < times[2]  # retired after 1, 2 and 3 rounds
     assert rep["p50_s"] == times[1] and rep["mean_s"] == pytest.approx(sum(times) / 3)
+
+
+def test_latency_report_keeps_capped_requests_apart(fake):
+    """Percentiles of time to tolerance cover only the requests that reached
+    it; a request stopped by the attempt limit is counted and timed apart."""
+    srv = serving.Server(round_attempts=10, iter_limit=40, memory_budget=10 ** 9, clock=fake)
+    for k in (5, 15, 1000):
+        srv.submit(FakeLP(k), arrival=0.0)
+    srv.drain()
+    rep = srv.latency_report()
+    solved = sorted(r.time_to_tol for r in srv.done.values() if r.status == LP_OPTIMAL)
+    capped = [r.time_to_tol for r in srv.done.values() if r.status != LP_OPTIMAL]
+    assert rep["finished"] == 3 and rep["reached_tol"] == 2 and rep["stopped_before_tol"] == 1
+    assert len(capped) == 1 and capped[0] > solved[-1]  # stopped after 4 rounds
+    assert rep["p99_s"] <= solved[-1] and rep["mean_s"] == pytest.approx(sum(solved) / 2)
+    assert rep["stopped_p50_s"] == capped[0]
