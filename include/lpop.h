@@ -114,14 +114,17 @@ typedef struct lp_options {
   void* stream;              /* cudaStream_t every launch and copy goes to; NULL = default stream */
   int32_t precision;         /* LP_PREC_*; default LP_PREC_FP64 */
   double refine_tol;         /* mixed: the FP32 phase hands over to FP64 once the relative KKT
-                                error is at most this, or after 3 checks without a 10% gain;
-                                default 1e-6 */
+                                error is at most this (or after refine_stall checks without a
+                                10% gain, below); default 1e-6 */
   lp_device_alloc_fn device_alloc; /* NULL: cudaMalloc.  A problem takes its buffers from one block of
                                       lp_memory_bytes() bytes (the per-device step-size table, 16 MiB,
                                       shared by all problems, always comes from cudaMalloc) */
   lp_device_free_fn device_free;   /* required exactly when device_alloc is set */
   void* alloc_ctx;                 /* passed to device_alloc and device_free */
-  int32_t reserved[2];             /* must be zero */
+  int32_t refine_stall;            /* mixed: the FP32 phase also hands over after this many checks in a
+                                      row without a 10% drop of its best relative KKT error; >= 1,
+                                      default 16 */
+  int32_t reserved;                /* must be zero */
 } lp_options;
 
 typedef struct lp_stats {

@@ -65,7 +65,8 @@ class LpOptions(ctypes.Structure):
         ("device_alloc", c_void_p),
         ("device_free", c_void_p),
         ("alloc_ctx", c_void_p),
-        ("reserved", c_int32 * 2),
+        ("refine_stall", c_int32),
+        ("reserved", c_int32),
     ]
 
 

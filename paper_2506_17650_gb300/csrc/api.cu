@@ -189,10 +189,10 @@ int check_options(const lp_options& o, std::string& msg) {
   if (o.precision != LP_PREC_FP64 && o.precision != LP_PREC_MIXED) return msg = "unknown precision", 1;
   if (o.kernel_timing < 0) return msg = "kernel_timing must be >= 0", 1;
   if (!(o.refine_tol >= 0.0)) return msg = "refine_tol must be >= 0", 1;
+  if (o.refine_stall < 1) return msg = "refine_stall must be >= 1", 1;
   if ((o.device_alloc == nullptr) != (o.device_free == nullptr))
     return msg = "device_alloc and device_free must be given together", 1;
-  for (int i = 0; i < 2; ++i)
-    if (o.reserved[i] != 0) return msg = "reserved option fields must be zero", 1;
+  if (o.reserved != 0) return msg = "the reserved option field must be zero", 1;
   return 0;
 }
 
@@ -680,8 +680,8 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
       return set_err(nullptr, LP_ERR_INVALID_INPUT,
                      "bounds of variable " + std::to_string(j) + " are invalid (need lb <= ub, lb < inf, ub > -inf)");
   }
-  // FP64 rows take one lane up to 16 entries whatever the matrix size: extra
-  // lanes cost FP64 shuffle adds, which outweigh the added parallelism on GB300
+  // FP64 rows take one lane up to kSellMaxLen entries whatever the matrix size:
+  // extra lanes cost FP64 shuffle adds, which outweigh the added parallelism on GB300
   HostLayout lay;
   int rc = build_layout(m, n, nnz, row_ptr, col_idx, val, lay, msg, 0);
   if (rc != LP_OK) return set_err(nullptr, rc, msg);
@@ -730,6 +730,7 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
   p->prm.alpha = o.alpha;
   p->prm.floor = o.precond_floor;
   p->prm.refine_tol = o.refine_tol;
+  p->prm.refine_stall = o.refine_stall;
   {
     int64_t bytes = 0;
     if (lp_memory_bytes(m, n, lay.nnz, &o, &bytes) == LP_OK && bytes > 0) {
@@ -773,7 +774,7 @@ int read_kkt(lp_problem* p, double* kkt) {
 }
 
 // Mixed precision: after a check in the FP32 phase, hand over to FP64 once the
-// relative KKT error is at most refine_tol or after 3 checks without a 10% gain.
+// relative KKT error is at most refine_tol or after refine_stall checks without a 10% gain.
 int maybe_refine(lp_problem* p) {
   if (!p->fp32_phase) return LP_OK;
   double kkt = 0.0;
@@ -784,7 +785,7 @@ int maybe_refine(lp_problem* p) {
   } else {
     p->stall += 1;
   }
-  if (kkt <= p->opt.refine_tol || p->stall >= 3 || !std::isfinite(kkt)) {
+  if (kkt <= p->opt.refine_tol || p->stall >= p->opt.refine_stall || !std::isfinite(kkt)) {
     launch_promote_state(p->d, p->stream);
     CK(cudaGetLastError());
     *p->h_status = 0;
@@ -948,6 +949,7 @@ void lp_options_default(lp_options* o) {
   o->stream = nullptr;
   o->precision = LP_PREC_FP64;
   o->refine_tol = 1e-6;
+  o->refine_stall = 16;
 }
 
 const char* lp_last_error(const lp_problem* p) {
@@ -1090,8 +1092,9 @@ int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, in
   const long long S = nnz / 4096 + 1;
   t += 2 * (r(8LL * 2 * S) + r(16LL * 2 * S) + r(4LL * S));
   t += 2 * r(8LL * kMaxPartials * (4096 + S));  // per-block records (upper bound of the grid) and row slots
-  // sliced copies of the rows of up to 16 entries (at most nnz entries plus the padding of 17 bins' last slices)
-  const long long SE = nnz + 17LL * 31 * 16;
+  // sliced copies of the rows of up to kSellMaxLen entries (at most nnz entries plus the
+  // padding of the last slices of kSellMaxLen + 1 bins)
+  const long long SE = nnz + (kSellMaxLen + 1LL) * 31 * kSellMaxLen;
   t += 2 * (r(4LL * SE) + r(8LL * SE) + (o.precision == LP_PREC_MIXED ? r(4LL * SE) : 0));
   *bytes = t;
   return LP_OK;

@@ -272,7 +272,7 @@ __device__ bool team_round(const Member& mb, DevState& s, int& budget, int rank,
       }
       if (s.status != 0) break;
       if (sizeof(V) == sizeof(float) && s.phase32) {
-        // mixed precision hand-over: at refine_tol, or after 3 checks without a 10% gain
+        // mixed precision hand-over: at refine_tol, or after refine_stall checks without a 10% gain
         if (threadIdx.x == 0) {
           const double kkt = fmax(s.rel_pres, fmax(s.rel_dres, s.rel_gap));
           if (kkt < 0.9 * s.best_kkt) {
@@ -281,7 +281,7 @@ __device__ bool team_round(const Member& mb, DevState& s, int& budget, int rank,
           } else {
             s.stall += 1;
           }
-          if (kkt <= prm.refine_tol || s.stall >= 3 || !isfinite(kkt)) s.phase32 = 0;
+          if (kkt <= prm.refine_tol || s.stall >= prm.refine_stall || !isfinite(kkt)) s.phase32 = 0;
         }
         __syncthreads();
         if (!s.phase32) {

@@ -48,6 +48,7 @@ struct Params {
   double b_norm;  // ||b||_2, user units
   double c_norm;  // ||c||_2, user units
   double refine_tol;  // mixed precision: FP32 -> FP64 hand-over threshold
+  int refine_stall;   // ... or after this many checks without a 10% KKT gain
 };
 
 // Device-resident solver state.  Written only by single-thread control code

@@ -104,12 +104,15 @@ std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<
 
 }  // namespace
 
-// Lanes per row.  Short rows get one lane each: on GB300 the FP64 pipe, not
-// memory, limits these kernels, and one lane per row needs no shuffle adds to
-// combine lane sums.  Longer rows split over 4..32 lanes for coalescing.
+// Lanes per row.  Rows of up to kSellMaxLen entries get one lane each, from
+// the sliced copy (every load of a warp contiguous): on GB300 the FP64 pipe
+// limits these kernels, and one lane per row needs no shuffle adds to combine
+// lane sums and runs the row's epilogue on every lane (with W lanes per row
+// the epilogue's FP64 instructions run on one lane in W).  Longer rows split
+// over 4..32 lanes.
 int width_for_length(long long len, int widen) {
   int w;
-  if (len <= 16) w = 1;
+  if (len <= kSellMaxLen) w = 1;
   else if (len <= 64) w = 4;
   else if (len <= 256) w = 16;
   else if (len <= kBlockRowThreshold) w = 32;
@@ -130,10 +133,12 @@ BinTable make_bins(const std::vector<int>& widths_sorted, const std::vector<int>
   int r = 0;
   while (r < rows) {
     const int w = widths_sorted[r];
-    // one-lane rows (at most 16 entries) go to sliced bins of one exact length
+    // one-lane rows (at most kSellMaxLen entries) go to sliced bins of one exact length
     const bool sliced = w == 1 && !lengths_sorted.empty();
     int e = r;
     while (e < rows && widths_sorted[e] == w && (!sliced || lengths_sorted[e] == lengths_sorted[r])) ++e;
+    // at most kSellMaxLen + 1 sliced lengths and six other classes: within kMaxBins
+    static_assert(kSellMaxLen + 1 + 6 + 1 <= kMaxBins, "bin table too small");
     Bin& b = t.bin[t.nbins++];
     b.row_begin = r;
     b.row_end = e;

@@ -6,7 +6,8 @@
 namespace lpop {
 
 constexpr int kBlock = 256;      // threads per block of every row kernel
-constexpr int kMaxBins = 28;     // row-length classes per matrix
+constexpr int kMaxBins = 64;     // row-length classes per matrix
+constexpr int kSellMaxLen = 48;  // rows of at most this many entries take one lane, from the sliced copy
 constexpr int kMaxPartials = 20; // fields of a partial-sum record (an A-row kernel's own + the folded A^T-row ones)
 constexpr int kPrimalTimed = 0;  // kernel ids for the event timers
 constexpr int kDualTimed = 1;
@@ -19,7 +20,7 @@ enum Sched : int { kAdagrad = 0, kAdagradNorm = 1, kConst = 2 };
 // handled with `width` lanes per row (1..32), a whole block per row when
 // width == 0, cut into segments of seg_len entries that different blocks
 // reduce concurrently when width == kSegmented, or, when width == kSell, rows
-// of exactly `len` entries (len <= 16) read from a sliced copy: slices of 32
+// of exactly `len` entries (len <= kSellMaxLen) read from a sliced copy: slices of 32
 // consecutive rows stored column-major (entry k of the slice's row t at
 // base + slice * 32 len + 32 k + t), so every load of a warp is contiguous
 // and an entry's position needs no row pointer.  Work units: one row per unit

@@ -27,6 +27,7 @@ from tests.conftest import ROOT
 
 CSRC = os.path.join(ROOT, "paper_2506_17650_gb300", "csrc")
 K_SEGMENTED, K_SELL, K_BLOCK = -1, -2, 256
+K_SELL_MAX = 48  # rows of at most this many entries are sliced (kSellMaxLen of the layout)
 
 
 @pytest.fixture(scope="module")
@@ -105,7 +106,7 @@ def check_bins(bt, rp, rows):
         else:
             unit += -(-(b["row_end"] - b["row_begin"]) // rows_per_unit(w))
         if w == K_SELL:
-            assert np.all(seg == b["len"]) and 0 <= b["len"] <= 16  # empty rows form a bin of length 0
+            assert np.all(seg == b["len"]) and 0 <= b["len"] <= K_SELL_MAX  # empty rows form a bin of length 0
             assert b["base"] == sliced
             sliced += -(-(b["row_end"] - b["row_begin"]) // 32) * 32 * b["len"]
         elif w == 0:
