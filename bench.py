@@ -248,15 +248,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_bytes(m, n, nnz):
-    """Algorithmic bytes per launch of the two step kernels (FP64 values, int32 indices).
+def kernel_bytes(m, n, nnz, vb=8):
+    """Algorithmic bytes per launch of the two step kernels, values of vb bytes
+    (8: FP64; 4: the FP32 phase of mixed precision), int32 indices.
 
-    primal step: CSR(A^T) 12 nnz + 4 n, gathered y 8 m, c, l, u, T, x read + x+ written
-                 + average read/write = 8 n * 8
-    dual step:   CSR(A) 12 nnz + 4 m, gathered x+ 8 n, b, Sigma, y, Ax read, y+, Ax+
-                 written, average read/write = 8 m * 8, sense 1 m"""
-    primal = 12 * nnz + 4 * n + 8 * m + 64 * n
-    dual = 12 * nnz + 4 * m + 8 * n + 65 * m
+    primal step: CSR(A^T) (4 + vb) nnz + 4 n, gathered y vb m, c, l, u, T, x read + x+
+                 written + average read/write = 8 vb n
+    dual step:   CSR(A) (4 + vb) nnz + 4 m, gathered x+ vb n, b, Sigma, y, Ax read, y+,
+                 Ax+ written, average read/write = 8 vb m, sense 1 m"""
+    primal = (4 + vb) * nnz + 4 * n + vb * m + 8 * vb * n
+    dual = (4 + vb) * nnz + 4 * m + vb * n + 8 * vb * m + m
     return primal, dual
 
 
@@ -265,8 +266,7 @@ def kernel_bytes(m, n, nnz):
 # smaller instance of the same workload is scaled by the algorithmic bytes
 # (the units processed).  Re-take a capture whenever the kernel changes.
 NCU_TRAFFIC = {
-    ("transport", "dual"): (9_040_128, 9_850_000, "profiles/transport_dual_step_full.md"),
-    ("powerlaw", "primal"): (66_406_912, 70_898_060, "profiles/powerlaw_primal_step_full.md (scale 0.1)"),
+    ("transport", "dual", "double"): (9_040_128, 9_850_000, "profiles/transport_dual_step_full.md"),
 }
 
 
@@ -352,7 +352,7 @@ def budget_run(lpop, torch, prob, stream, tol, budget, kkt_dir=None, name=None):
 
 
 def roofline(kind, m, n, nnz, kt_ms, kt_n, clk, label):
-    pb, db = kernel_bytes(m, n, nnz)
+    pb, db = kernel_bytes(m, n, nnz, 4 if label == "float" else 8)
     pf64, df64 = kernel_fp64_ops(m, n, nnz)
     avg_primal_ms = kt_ms[0] / max(kt_n[0], 1)
     avg_dual_ms = kt_ms[1] / max(kt_n[1], 1)
@@ -365,7 +365,7 @@ def roofline(kind, m, n, nnz, kt_ms, kt_n, clk, label):
     sm_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
     fp64_peak = SMS * FP64_LANES_PER_SM_CLK * sm_clk / 1e9
     fp64_achieved = dom_ops / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
-    traffic = NCU_TRAFFIC.get((kind, dom))
+    traffic = NCU_TRAFFIC.get((kind, dom, label))
     return {
         "bound": "hbm",
         "kernel": f"{dom}_step_kernel<{label}> (fused sparse product + update)",

@@ -8,6 +8,7 @@ namespace lpop {
 constexpr int kBlock = 256;      // threads per block of every row kernel
 constexpr int kMaxBins = 64;     // row-length classes per matrix
 constexpr int kSellMaxLen = 48;  // rows of at most this many entries take one lane, from the sliced copy
+constexpr int kPairMaxLen = 2;   // sliced rows of at most this many entries: two rows per thread
 constexpr int kMaxPartials = 20; // fields of a partial-sum record (an A-row kernel's own + the folded A^T-row ones)
 constexpr int kPrimalTimed = 0;  // kernel ids for the event timers
 constexpr int kDualTimed = 1;
@@ -25,8 +26,8 @@ enum Sched : int { kAdagrad = 0, kAdagradNorm = 1, kConst = 2 };
 // base + slice * 32 len + 32 k + t), so every load of a warp is contiguous
 // and an entry's position needs no row pointer.  Work units: one row per unit
 // for width 0, kBlock/width rows per unit for 1..32, one segment per unit for
-// kSegmented, kBlock rows per unit for kSell; units of all bins are numbered
-// consecutively.
+// kSegmented, kBlock rows per unit for kSell (2 kBlock, two rows per thread,
+// when len <= kPairMaxLen); units of all bins are numbered consecutively.
 constexpr int kSegmented = -1;
 constexpr int kSell = -2;
 
@@ -42,7 +43,7 @@ struct Bin {
 // Rows per work unit of a bin.
 inline int rows_per_unit(const Bin& b) {
   if (b.width == 0 || b.width == kSegmented) return 1;
-  if (b.width == kSell) return kBlock;
+  if (b.width == kSell) return b.len <= kPairMaxLen ? 2 * kBlock : kBlock;
   return kBlock / b.width;
 }
 

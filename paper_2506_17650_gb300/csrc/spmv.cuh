@@ -5,11 +5,12 @@
 //     s[q] = sum_k M.v[k] * x_q[M.ci[k]],   k in [M.rp[r], M.rp[r+1])
 // in the accumulator type Acc (matrix and vectors of type V) and hands them to
 // op.row(r, s); op.prefetch(r) is called first, before the row's loads, so an
-// op can start loading its own per-row operands early.  Rows up to 16 entries
-// use one lane, longer rows 4..32 lanes that stride through the row so that
-// one warp's loads of M.v and M.ci are contiguous, long rows a whole block,
-// and the longest rows several blocks (segments).  Lane sums are combined by a fixed
-// shuffle tree, so results do not depend on scheduling.
+// op can start loading its own per-row operands early.  Rows up to 48 entries
+// use one lane (two rows per thread up to 2 entries) and read a sliced copy,
+// longer rows 4..32 lanes that stride through the row so that one warp's loads
+// of M.v and M.ci are contiguous, long rows a whole block, and the longest rows
+// several blocks (segments).  Lane sums are combined by a fixed shuffle tree,
+// so results do not depend on scheduling.
 #pragma once
 
 #include <type_traits>
@@ -22,6 +23,12 @@ template <int NV, class V>
 struct Gather {
   const V* x[NV];
 };
+
+// Ops that keep per-block reduction accumulators (member `acc`).
+template <class Op, class = void>
+struct HasAcc : std::false_type {};
+template <class Op>
+struct HasAcc<Op, std::void_t<decltype(std::declval<Op&>().acc)>> : std::true_type {};
 
 // Entries handled per lane per round: all their index/value loads are issued,
 // then all gathers, then the FMAs, so each lane keeps kChunk independent
@@ -131,6 +138,71 @@ __device__ __forceinline__ void sell_rows(const BinTable& bt, const Bin& B, int 
   op.row(row, s);
 }
 
+// A unit of a kSell bin of at most kPairMaxLen entries per row: thread t
+// takes rows i and i + kBlock of the unit's 2 kBlock rows, and every load of
+// both rows (operands, entries, gathers) is issued before either row's
+// arithmetic, so that the two rows' FP64 chains interleave.  The second row's
+// reduction terms are kept apart and added to the thread's accumulators after
+// the pair (a fixed order).
+template <int NV, class V, class Acc, class Op>
+__device__ __forceinline__ void sell_rows_pair(const BinTable& bt, const Bin& B, int local, const Gather<NV, V>& g,
+                                               Op& op) {
+  constexpr int C = kPairMaxLen;
+  const int i0 = local * (2 * kBlock) + (int)threadIdx.x;
+  const int i1 = i0 + kBlock;
+  const int r0 = B.row_begin + i0, r1 = B.row_begin + i1;
+  if (r0 >= B.row_end) return;
+  const bool v1 = r1 < B.row_end;
+  Op op2 = op;
+  if constexpr (HasAcc<Op>::value) {
+    constexpr int NA = (int)(sizeof(op.acc) / sizeof(op.acc[0]));
+#pragma unroll
+    for (int q = 0; q < NA; ++q) op2.acc[q] = 0;
+  }
+  op.prefetch(r0);
+  if (v1) op2.prefetch(r1);
+  const int L = B.len;
+  const long long o0 = B.base + (long long)(i0 >> 5) * (32LL * L) + (i0 & 31);
+  const long long o1 = B.base + (long long)(i1 >> 5) * (32LL * L) + (i1 & 31);
+  const int* sci = bt.sell_ci;
+  const V* sv = sell_values<V>(bt);
+  int c0[C], c1[C];
+  Acc a0[C], a1[C];
+#pragma unroll
+  for (int u = 0; u < C; ++u) {
+    const bool ok = u < L;
+    c0[u] = ok ? __ldg(sci + o0 + 32 * u) : 0;
+    a0[u] = ok ? (Acc)__ldg(sv + o0 + 32 * u) : Acc(0);
+    c1[u] = ok && v1 ? __ldg(sci + o1 + 32 * u) : 0;
+    a1[u] = ok && v1 ? (Acc)__ldg(sv + o1 + 32 * u) : Acc(0);
+  }
+  Acc s0[NV], s1[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    Acc x0[C], x1[C];
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      x0[u] = u < L ? (Acc)__ldg(g.x[q] + c0[u]) : Acc(0);
+      x1[u] = u < L && v1 ? (Acc)__ldg(g.x[q] + c1[u]) : Acc(0);
+    }
+    s0[q] = Acc(0);
+    s1[q] = Acc(0);
+#pragma unroll
+    for (int u = 0; u < C; ++u) {
+      if (u >= L) break;
+      s0[q] = fma(a0[u], x0[u], s0[q]);
+      s1[q] = fma(a1[u], x1[u], s1[q]);
+    }
+  }
+  op.row(r0, s0);
+  if (v1) op2.row(r1, s1);
+  if constexpr (HasAcc<Op>::value) {
+    constexpr int NA = (int)(sizeof(op.acc) / sizeof(op.acc[0]));
+#pragma unroll
+    for (int q = 0; q < NA; ++q) op.acc[q] += op2.acc[q];
+  }
+}
+
 // Block-wide FP64 sums of the entries [beg, end) of one row (valid in warp 0).
 template <int NV, class V, class Acc>
 __device__ __forceinline__ void block_dot(int beg, int end, const CsrT<V>& M, const Gather<NV, V>& g, double (&s)[NV],
@@ -185,11 +257,6 @@ __device__ __forceinline__ void row_into_slot(Op& op, int row, const Acc (&r)[NV
   for (int q = NA; q < kMaxPartials; ++q) slot[q] = 0.0;  // fields read by wider sums
 }
 
-// Ops that keep per-block reduction accumulators (member `acc`).
-template <class Op, class = void>
-struct HasAcc : std::false_type {};
-template <class Op>
-struct HasAcc<Op, std::void_t<decltype(std::declval<Op&>().acc)>> : std::true_type {};
 
 // One segment of a segmented row, published for the row's other segments;
 // the block that completes the row's last segment adds the segment sums in
@@ -261,8 +328,18 @@ __device__ __forceinline__ void for_each_row_range(const BinTable& bt, const Csr
     switch (bt.bin[b].width) {
       case kSegmented: segment_unit<NV, V, Acc>(bt, local, M, g, op, smem, row_slots); break;
       case kSell:
-        if (bt.sell_ci) sell_rows<NV, V, Acc>(bt, bt.bin[b], local, g, op);
-        else vec_rows<1, NV, V, Acc>(row_begin + local * kBlock, row_end, M, g, op);
+        if (bt.bin[b].len <= kPairMaxLen) {  // units of 2 kBlock rows
+          if (bt.sell_ci) {
+            sell_rows_pair<NV, V, Acc>(bt, bt.bin[b], local, g, op);
+          } else {
+            vec_rows<1, NV, V, Acc>(row_begin + local * 2 * kBlock, row_end, M, g, op);
+            vec_rows<1, NV, V, Acc>(row_begin + local * 2 * kBlock + kBlock, row_end, M, g, op);
+          }
+        } else if (bt.sell_ci) {
+          sell_rows<NV, V, Acc>(bt, bt.bin[b], local, g, op);
+        } else {
+          vec_rows<1, NV, V, Acc>(row_begin + local * kBlock, row_end, M, g, op);
+        }
         break;
       case 0: block_row<NV, V, Acc>(row_begin + local, M, g, op, smem); break;
       case 1: vec_rows<1, NV, V, Acc>(row_begin + local * kBlock, row_end, M, g, op); break;

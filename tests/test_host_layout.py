@@ -28,6 +28,7 @@ from tests.conftest import ROOT
 CSRC = os.path.join(ROOT, "paper_2506_17650_gb300", "csrc")
 K_SEGMENTED, K_SELL, K_BLOCK = -1, -2, 256
 K_SELL_MAX = 48  # rows of at most this many entries are sliced (kSellMaxLen of the layout)
+K_PAIR_MAX = 2  # sliced rows of at most this many entries: units of two rows per thread (kPairMaxLen)
 
 
 @pytest.fixture(scope="module")
@@ -83,9 +84,11 @@ def run_layout(runner, tmp_path, m, n, rp, ci, v, target=0, seg_len=0):
     return lay
 
 
-def rows_per_unit(width):
+def rows_per_unit(width, length=None):
     if width in (0, K_SEGMENTED):
         return 1
+    if width == K_SELL and length is not None and length <= K_PAIR_MAX:
+        return 2 * K_BLOCK
     if width == K_SELL:
         return K_BLOCK
     return K_BLOCK // width
@@ -104,7 +107,7 @@ def check_bins(bt, rp, rows):
             nseg = int(np.sum((seg + bt["seg_len"] - 1) // bt["seg_len"]))
             unit += nseg
         else:
-            unit += -(-(b["row_end"] - b["row_begin"]) // rows_per_unit(w))
+            unit += -(-(b["row_end"] - b["row_begin"]) // rows_per_unit(w, b["len"]))
         if w == K_SELL:
             assert np.all(seg == b["len"]) and 0 <= b["len"] <= K_SELL_MAX  # empty rows form a bin of length 0
             assert b["base"] == sliced
