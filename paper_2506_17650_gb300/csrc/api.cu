@@ -367,6 +367,8 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
   d.f64.Atv = d.At_v;
   TRY(dalloc(p, &d.dr, m));
   TRY(dalloc(p, &d.dc, n));
+  TRY(dalloc(p, &d.inv_dr, m));
+  TRY(dalloc(p, &d.inv_dc, n));
   TRY(alloc_vecs(p, d.f64, m, n, false));
   if (p->mixed) TRY(alloc_vecs(p, d.f32, m, n, true));
   TRY(dalloc(p, &d.work2, (size_t)(m > n ? m : n) + 1));
@@ -1084,7 +1086,7 @@ int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, in
   auto r = [](long long b) { return ((b < 8 ? 8 : b) + 255) / 256 * 256; };
   long long t = 0;
   t += r(4LL * (m + 1)) + 2 * r(4LL * nnz) + 2 * r(8LL * nnz) + r(4LL * (n + 1));  // CSR of A and A^T
-  t += r(8LL * m) + r(8LL * n);                                                    // dr, dc
+  t += 2 * (r(8LL * m) + r(8LL * n));                                              // dr, dc and reciprocals
   t += 13 * r(8LL * m) + 12 * r(8LL * n);                                          // FP64 vector set
   if (o.precision == LP_PREC_MIXED) t += 2 * r(4LL * nnz) + 13 * r(4LL * m) + 12 * r(4LL * n);  // FP32 set
   t += r(8LL * (m > n ? m : n) + 8) + r(m) + r(8LL * ((long long)m + n + 2048)) + r(sizeof(DevState));

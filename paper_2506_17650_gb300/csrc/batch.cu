@@ -104,9 +104,9 @@ __device__ void team_check(const Dev& d, const Params& prm, DevState& s, int ran
   double p1[10], p2[8];
   if (prm.mode == kPdlp) {
     CheckPrimalOp<2, V> op;
-    op.c = v.c; op.l = v.l; op.u = v.u; op.dc = d.dc;
+    op.c = v.c; op.l = v.l; op.u = v.u; op.inv_dc = d.inv_dc;
     op.xc = v.x[cur]; op.xbarc = v.xbar[cur]; op.xlast = v.x_last;
-    op.w = s.wsum;
+    op.inv_w = s.wsum > 0.0 ? 1.0 / s.wsum : 0.0;
     op.avg = avg;
 #pragma unroll
     for (int q = 0; q < 10; ++q) op.acc[q] = 0.0;
@@ -118,9 +118,9 @@ __device__ void team_check(const Dev& d, const Params& prm, DevState& s, int ran
     for (int q = 0; q < 10; ++q) p1[q] = op.acc[q];
   } else {
     CheckPrimalOp<1, V> op;
-    op.c = v.c; op.l = v.l; op.u = v.u; op.dc = d.dc;
+    op.c = v.c; op.l = v.l; op.u = v.u; op.inv_dc = d.inv_dc;
     op.xc = v.x[cur]; op.xbarc = v.xbar[cur]; op.xlast = v.x_last;
-    op.w = s.wsum;
+    op.inv_w = s.wsum > 0.0 ? 1.0 / s.wsum : 0.0;
     op.avg = 0;
 #pragma unroll
     for (int q = 0; q < 10; ++q) op.acc[q] = 0.0;
@@ -133,10 +133,10 @@ __device__ void team_check(const Dev& d, const Params& prm, DevState& s, int ran
   team_reduce<10>(p1, blk, slots + 7, T, wide);
   {
     CheckDualOp<V> op;
-    op.b = v.b; op.dr = d.dr; op.sense = d.sense;
+    op.b = v.b; op.inv_dr = d.inv_dr; op.sense = d.sense;
     op.axc = v.ax[cur]; op.yc = v.y[cur]; op.ybarc = v.ybar[cur]; op.ylast = v.y_last;
     op.ax_avg = v.ax_avg;
-    op.w = s.wsum;
+    op.inv_w = s.wsum > 0.0 ? 1.0 / s.wsum : 0.0;
     op.avg = avg;
 #pragma unroll
     for (int q = 0; q < 8; ++q) op.acc[q] = 0.0;

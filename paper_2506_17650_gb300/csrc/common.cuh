@@ -138,6 +138,7 @@ struct Dev {
   int *A_rp, *A_ci, *At_rp, *At_ci;
   double *A_v, *At_v;  // == f64.Av, f64.Atv
   double *dr, *dc;     // A~ = diag(dr) A diag(dc)
+  double *inv_dr, *inv_dc;  // 1 / dr, 1 / dc (the KKT checks' user-unit residuals)
   uint8_t* sense;
   Vecs<double> f64;
   Vecs<float> f32;    // null pointers unless mixed precision

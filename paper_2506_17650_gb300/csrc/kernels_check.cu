@@ -36,10 +36,11 @@ __global__ void __launch_bounds__(kBlock, kCheckBlocksPerSm<V>) check_primal_ker
   const DevState* st = d.st;
   const int cur = st->cur;
   CheckPrimalOp<NV, V> op;
-  op.c = v.c; op.l = v.l; op.u = v.u; op.dc = d.dc;
+  op.c = v.c; op.l = v.l; op.u = v.u; op.inv_dc = d.inv_dc;
   op.xc = v.x[cur]; op.xbarc = v.xbar[cur]; op.xlast = v.x_last;
-  op.w = st->wsum;
-  op.avg = AVG && op.w > 0.0;
+  const double w = st->wsum;
+  op.avg = AVG && w > 0.0;
+  op.inv_w = op.avg ? 1.0 / w : 0.0;
 #pragma unroll
   for (int q = 0; q < 10; ++q) op.acc[q] = 0.0;
   Gather<NV, V> g;
@@ -67,10 +68,10 @@ __global__ void __launch_bounds__(kBlock, kCheckBlocksPerSm<V>) check_dual_kerne
   const double w = st->wsum;
   const int avg_ok = AVG && w > 0.0;
   CheckDualOp<V> op;
-  op.b = v.b; op.dr = d.dr; op.sense = d.sense;
+  op.b = v.b; op.inv_dr = d.inv_dr; op.sense = d.sense;
   op.axc = v.ax[cur]; op.yc = v.y[cur]; op.ybarc = v.ybar[cur]; op.ylast = v.y_last;
   op.ax_avg = v.ax_avg;
-  op.w = w;
+  op.inv_w = avg_ok ? 1.0 / w : 0.0;
   op.avg = avg_ok;
 #pragma unroll
   for (int q = 0; q < 8; ++q) op.acc[q] = 0.0;

@@ -135,12 +135,16 @@ __global__ void factor_mul_kernel(double* fr, double* dr, int m, double* fc, dou
 __global__ void scale_vectors_kernel(Dev d) {
   const Vecs<double>& v = d.f64;
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) v.b[i] = d.dr[i] * v.b[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.m; i += stride) {
+    v.b[i] = d.dr[i] * v.b[i];
+    d.inv_dr[i] = 1.0 / d.dr[i];
+  }
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += stride) {
     const double f = d.dc[j];
     v.c[j] = f * v.c[j];
     v.l[j] = v.l[j] / f;
     v.u[j] = v.u[j] / f;
+    d.inv_dc[j] = 1.0 / f;
   }
 }
 

@@ -259,10 +259,11 @@ __device__ inline void step_control_state(DevState& s, const Params& prm, double
 template <int NV, class V>
 struct CheckPrimalOp {
   const V *c, *l, *u, *xc, *xbarc, *xlast;
-  const double* dc;
-  double w;
+  const double* inv_dc;  // 1 / dc: user-unit dual residuals without a division per row
+  double inv_w;          // 1 / (average weight)
   int avg;
   double acc[10];
+  static constexpr bool kNoPair = true;  // one row per thread: no second set of 10 accumulators
   __device__ __forceinline__ void prefetch(int) {}
 
   __device__ __forceinline__ void side(int j, double rc, double x, double* a) {
@@ -274,7 +275,7 @@ struct CheckPrimalOp {
     else if (uf) lam = fmin(rc, 0.0);
     else lam = 0.0;
     const double ds = rc - lam;
-    const double du = ds / __ldg(dc + j);
+    const double du = ds * __ldg(inv_dc + j);
     a[0] += du * du;
     a[1] += ds * ds;
     a[2] += (lf ? lo * fmax(lam, 0.0) : 0.0) - (uf ? hi * fmax(-lam, 0.0) : 0.0);
@@ -286,19 +287,20 @@ struct CheckPrimalOp {
   __device__ __forceinline__ void row(int j, const double (&s)[NV]) {
     const double cj = (double)__ldg(c + j);
     side(j, cj - s[0], (double)xc[j], acc);
-    if (NV > 1 && avg) side(j, cj - s[NV - 1] / w, (double)xbarc[j] / w, acc + 5);
+    if (NV > 1 && avg) side(j, cj - s[NV - 1] * inv_w, (double)xbarc[j] * inv_w, acc + 5);
   }
 };
 
 template <class V>
 struct CheckDualOp {
   const V *b, *axc, *yc, *ybarc, *ylast;
-  const double* dr;
+  const double* inv_dr;  // 1 / dr: user-unit primal residuals without a division per row
   const uint8_t* sense;
   V* ax_avg;
-  double w;
+  double inv_w;  // 1 / (average weight)
   int avg;
   double acc[8];
+  static constexpr bool kNoPair = true;
   __device__ __forceinline__ void prefetch(int) {}
 
   __device__ __forceinline__ void side(int i, double ax, double y, double* a) {
@@ -306,7 +308,7 @@ struct CheckDualOp {
     const double rs = ax - bi;
     const uint8_t sn = __ldg(sense + i);
     const double ps = sn == kEq ? rs : (sn == kGe ? fmax(-rs, 0.0) : fmax(rs, 0.0));
-    const double pu = ps / __ldg(dr + i);
+    const double pu = ps * __ldg(inv_dr + i);
     a[0] += pu * pu;
     a[1] += ps * ps;
     a[2] += bi * y;
@@ -318,9 +320,9 @@ struct CheckDualOp {
   __device__ __forceinline__ void row(int i, const double (&s)[1]) {
     side(i, (double)axc[i], (double)yc[i], acc);
     if (avg) {
-      const double axa = s[0] / w;
+      const double axa = s[0] * inv_w;
       ax_avg[i] = (V)axa;
-      side(i, axa, (double)ybarc[i] / w, acc + 4);
+      side(i, axa, (double)ybarc[i] * inv_w, acc + 4);
     }
   }
 };

@@ -30,6 +30,12 @@ struct HasAcc : std::false_type {};
 template <class Op>
 struct HasAcc<Op, std::void_t<decltype(std::declval<Op&>().acc)>> : std::true_type {};
 
+// Ops that take short sliced rows two per thread (all but those that declare kNoPair).
+template <class Op, class = void>
+struct AllowsPair : std::true_type {};
+template <class Op>
+struct AllowsPair<Op, std::void_t<decltype(Op::kNoPair)>> : std::false_type {};
+
 // Entries handled per lane per round: all their index/value loads are issued,
 // then all gathers, then the FMAs, so each lane keeps kChunk independent
 // loads in flight instead of one dependent load chain per entry.
@@ -97,14 +103,13 @@ __device__ __forceinline__ const double* sell_values<double>(const BinTable& bt)
 template <>
 __device__ __forceinline__ const float* sell_values<float>(const BinTable& bt) { return bt.sell_v32; }
 
-// A unit of a kSell bin: thread t takes row row_begin + local * kBlock + t, of
-// exactly B.len entries, from the sliced copy.  The loop bound is the same
-// for the whole warp and the loads of a warp are contiguous; the entries are
-// added in row order, as in the CSR path.
+// Row i of a kSell bin (row B.row_begin + i), of exactly B.len entries, from
+// the sliced copy.  Called by consecutive threads for consecutive rows, so the
+// loop bound is the same for the whole warp and the loads of a warp are
+// contiguous; the entries are added in row order, as in the CSR path.
 template <int NV, class V, class Acc, class Op>
-__device__ __forceinline__ void sell_rows(const BinTable& bt, const Bin& B, int local, const Gather<NV, V>& g,
-                                          Op& op) {
-  const int i = local * kBlock + (int)threadIdx.x;
+__device__ __forceinline__ void sell_rows_at(const BinTable& bt, const Bin& B, int i, const Gather<NV, V>& g,
+                                             Op& op) {
   const int row = B.row_begin + i;
   if (row >= B.row_end) return;
   op.prefetch(row);
@@ -136,6 +141,13 @@ __device__ __forceinline__ void sell_rows(const BinTable& bt, const Bin& B, int 
     }
   }
   op.row(row, s);
+}
+
+// A unit of a kSell bin: thread t takes row local * kBlock + t of the bin.
+template <int NV, class V, class Acc, class Op>
+__device__ __forceinline__ void sell_rows(const BinTable& bt, const Bin& B, int local, const Gather<NV, V>& g,
+                                          Op& op) {
+  sell_rows_at<NV, V, Acc>(bt, B, local * kBlock + (int)threadIdx.x, g, op);
 }
 
 // A unit of a kSell bin of at most kPairMaxLen entries per row: thread t
@@ -330,7 +342,13 @@ __device__ __forceinline__ void for_each_row_range(const BinTable& bt, const Csr
       case kSell:
         if (bt.bin[b].len <= kPairMaxLen) {  // units of 2 kBlock rows
           if (bt.sell_ci) {
-            sell_rows_pair<NV, V, Acc>(bt, bt.bin[b], local, g, op);
+            if constexpr (AllowsPair<Op>::value) {
+              sell_rows_pair<NV, V, Acc>(bt, bt.bin[b], local, g, op);
+            } else {  // the unit's two halves one after the other
+              const int i0 = local * 2 * kBlock + (int)threadIdx.x;
+              sell_rows_at<NV, V, Acc>(bt, bt.bin[b], i0, g, op);
+              sell_rows_at<NV, V, Acc>(bt, bt.bin[b], i0 + kBlock, g, op);
+            }
           } else {
             vec_rows<1, NV, V, Acc>(row_begin + local * 2 * kBlock, row_end, M, g, op);
             vec_rows<1, NV, V, Acc>(row_begin + local * 2 * kBlock + kBlock, row_end, M, g, op);

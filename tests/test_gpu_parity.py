@@ -261,6 +261,10 @@ def oracle_count_range(lp, o, tol, seeds=5, iter_limit=100_000):
 # objective is held to the distance two points at that tolerance can have.
 FULL_SOLVE_CASES = {"tiny_plain_norm_freq": True, "tiny_pdlp_freq": True, "mixed_pdlp_adagrad": True,
                     "rowmix_pdlp": True, "transport_small_pdlp": True, "powerlaw_tiny_pdlp": False}
+# Perturbed oracle solves that sample the count's spread: on the small power-law
+# LP the oracle's own count moves between 3,840 and 6,272 attempts over 31
+# perturbations of c at 1e-15, so five samples do not cover it.
+COUNT_SEEDS = {"powerlaw_tiny_pdlp": 30}
 
 
 @pytest.mark.parametrize("case", sorted(FULL_SOLVE_CASES))
@@ -277,7 +281,7 @@ def test_full_solve_matches_oracle(case):
             status_tight = p.solve(1e-8, 400_000)
             _, _, st_tight = p.result(want_x=False, want_y=False)
     assert status == res.status == lpop.LP_OPTIMAL
-    lo, hi = oracle_count_range(lp, o, 1e-4)
+    lo, hi = oracle_count_range(lp, o, 1e-4, seeds=COUNT_SEEDS.get(case, 5))
     assert 0.98 * lo <= st["iterations"] <= 1.02 * hi, (st["iterations"], lo, hi, res.iterations)
     assert max(st["rel_pres"], st["rel_dres"], st["rel_gap"]) <= 1e-4
     if FULL_SOLVE_CASES[case]:
