@@ -54,7 +54,9 @@ Readings of points the paper leaves open (each is a decision, not a quote):
 * R12 L2 rescaling (Section 4.2): rows and columns divided by the square root
   of their 2-norms.
 * R13 plain (vanilla) mode: T_0 = Sigma_0 = 1 with eta = 0.9 / ||A~||_2 fixed,
-  omega = ||c~|| / ||b~||, no restarts or averages.
+  omega = ||c~|| / ||b~||, no restarts or averages.  ||A~||_2 by power iteration
+  from the all-ones direction, restarted from a fixed +-1 vector (SplitMix64
+  signs of the column index) when A~ 1 = 0.
 """
 from __future__ import annotations
 
@@ -218,22 +220,44 @@ def l2_norm_rescale(A):
     return _apply(A, fr, fc), fr, fc
 
 
+def splitmix_signs(n):
+    """+1 or -1 for each index j < n: the top bit of SplitMix64 of j (the
+    generator of G. Steele, D. Lea and C. Flood, "Fast splittable pseudorandom
+    number generators", OOPSLA 2014: state j * 0x9E3779B97F4A7C15 after one
+    increment, then the two xor-shift-multiply rounds and a final xor-shift);
+    a set top bit gives -1.  Pinned by: hand values of the published mixer (tests)."""
+    with np.errstate(over="ignore"):
+        z = (np.arange(n, dtype=np.uint64) + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return np.where((z >> np.uint64(63)) != 0, -1.0, 1.0)
+
+
 def power_spectral_norm(A, iters):
     """||A||_2 by power iteration on A^T A from the all-ones direction:
     v <- w / ||w||, w = A^T A v, for ``iters`` rounds; returns sqrt(||w||) of the
-    last round.  Pinned by: agreement with the SVD norm (tests)."""
+    last round.  If the first product is exactly zero (every row of A sums to
+    zero, so the all-ones direction is in its null space), the iteration
+    starts again from the SplitMix64 sign vector (reading R13).  Pinned by:
+    agreement with the SVD norm, also on a matrix whose rows sum to zero (tests)."""
     n = A.shape[1]
     if n == 0 or A.nnz == 0:
         return 0.0
-    v = np.ones(n) / math.sqrt(n)
-    nw = 0.0
-    for _ in range(iters):
-        w = A.T @ (A @ v)
-        nw = float(np.linalg.norm(w))
-        if nw == 0.0:
+    for start in (np.ones(n), splitmix_signs(n)):
+        v = start / math.sqrt(n)
+        nw = 0.0
+        for it in range(iters):
+            w = A.T @ (A @ v)
+            nw = float(np.linalg.norm(w))
+            if nw == 0.0:
+                break
+            v = w / nw
+        if nw > 0.0:
+            return math.sqrt(nw)
+        if it > 0:  # only a zero first product restarts
             return 0.0
-        v = w / nw
-    return math.sqrt(nw)
+    return 0.0
 
 
 def scale_problem(lp, opts: Options) -> Scaled:

@@ -298,23 +298,40 @@ int preprocess(lp_problem* p) {
   if (p->opt.mode == LP_MODE_PDLP) {
     p->eta0 = p->amax > 0.0 ? 1.0 / p->amax : 1.0;
   } else {
-    // ||A~||_2 by power iteration on A~^T A~ from the all-ones direction
+    // ||A~||_2 by power iteration on A~^T A~ from the all-ones direction; if
+    // the first product is exactly zero (A~ 1 = 0), again from the +-1
+    // direction of SplitMix64 signs of the caller's column index
     double* v = d.f64.q;       // [n]
     double* t = d.f64.ax_avg;  // [m]
     double* w = fc;        // [n]
     p->norm_est = 0.0;
     if (p->nnz > 0) {
       launch_fill(v, 1.0 / std::sqrt((double)n), n, s);
+      bool restarted = false;
       for (int it = 0; it < p->opt.power_iters; ++it) {
         launch_spmv_binned(d.A, d.binsA, d.gridA, v, t, s);
         launch_spmv_binned(d.At, d.binsAt, d.gridAt, t, w, s);
         launch_norm2(w, n, red, s);
+        if (it == 0 && !restarted) {
+          const double nw0 = read_scalar(p, red, &rc);
+          TRY(rc);
+          if (nw0 == 0.0) {
+            std::vector<double> h(n);
+            const double sc = 1.0 / std::sqrt((double)n);
+            for (int j = 0; j < n; ++j) h[j] = splitmix_sign((unsigned long long)p->pcol[j]) * sc;
+            CK(cudaMemcpyAsync(v, h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+            CK(cudaStreamSynchronize(s));
+            restarted = true;
+            it = -1;
+            continue;
+          }
+        }
         launch_scale_by_inv(w, n, red, s);
         CK(cudaMemcpyAsync(v, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       }
       const double nw = read_scalar(p, red, &rc);
       TRY(rc);
-      p->norm_est = std::sqrt(nw);
+      p->norm_est = nw > 0.0 && std::isfinite(nw) ? std::sqrt(nw) : 0.0;
     }
     p->eta0 = p->norm_est > 0.0 ? p->opt.plain_step_factor / p->norm_est : 1.0;
   }

@@ -101,6 +101,18 @@ struct DevState {
   double best_kkt;
 };
 
+// +1 or -1 for index j from the top bit of SplitMix64 (Steele, Lea and Flood,
+// OOPSLA 2014) seeded so that output j is the generator's (j+1)-th: the
+// second start direction of the power iteration when the all-ones direction
+// lies in the null space of A.
+__host__ __device__ inline double splitmix_sign(unsigned long long j) {
+  unsigned long long z = (j + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return (z >> 63) ? -1.0 : 1.0;
+}
+
 // Entries of the step-size schedule table (attempt counts below this use the table).
 constexpr int kStepTab = 1 << 20;
 

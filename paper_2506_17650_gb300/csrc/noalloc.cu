@@ -52,6 +52,12 @@ int scratch_address(int dev, double** out) {
   return LP_OK;
 }
 
+// v[j] = scale * (+-1 from SplitMix64 of j): the power iteration's second start direction.
+__global__ void splitmix_fill_kernel(double* v, int n, double scale) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    v[j] = scale * splitmix_sign((unsigned long long)j);
+}
+
 }  // namespace
 }  // namespace lpop
 
@@ -95,10 +101,26 @@ extern "C" int lp_power_norm_noalloc(int32_t m, int32_t n, const int32_t* a_row_
   const Csr At{at_row_ptr, at_col_idx, at_val};
 
   launch_fill(v, 1.0 / std::sqrt((double)n), n, s);
+  bool restarted = false;
   for (int it = 0; it < iters; ++it) {
     launch_spmv_binned(A, ba, grid_a, v, t, s);
     launch_spmv_binned(At, bat, grid_at, t, w, s);
     launch_norm2(w, n, red, s);
+    if (it == 0 && !restarted) {
+      // a zero first product (every row of A sums to zero): start again from
+      // the SplitMix64 sign direction, as lp_create does
+      double nw0 = 0.0;
+      e = cudaMemcpyAsync(&nw0, red, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return fail(LP_ERR_CUDA, std::string("reading the norm failed: ") + cudaGetErrorString(e));
+      if (nw0 == 0.0) {
+        splitmix_fill_kernel<<<(n + kBlock - 1) / kBlock < 1024 ? (n + kBlock - 1) / kBlock : 1024, kBlock, 0, s>>>(
+            v, n, 1.0 / std::sqrt((double)n));
+        restarted = true;
+        it = -1;
+        continue;
+      }
+    }
     launch_scale_by_inv(w, n, red, s);
     double* tmp = v;  // the normalised w becomes the next v
     v = w;
@@ -110,6 +132,6 @@ extern "C" int lp_power_norm_noalloc(int32_t m, int32_t n, const int32_t* a_row_
   e = cudaMemcpyAsync(&nw, red, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(LP_ERR_CUDA, std::string("reading the result failed: ") + cudaGetErrorString(e));
-  *norm_out = std::sqrt(nw);
+  *norm_out = nw > 0.0 && std::isfinite(nw) ? std::sqrt(nw) : 0.0;
   return LP_OK;
 }

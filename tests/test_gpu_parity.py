@@ -426,6 +426,27 @@ def test_device_buffers_from_the_caller_allocator():
         assert np.array_equal(got[key], want[key]), key
 
 
+def test_plain_step_when_rows_sum_to_zero():
+    """Plain mode on rows x_i - x_{i+1} = 0 (a cycle; Ruiz and L2 rescaling
+    keep every row's sum at zero): the power iteration for ||A~||_2 restarts
+    from the SplitMix64 sign direction, on both sides, so eta_0 matches the
+    oracle's (instead of the fallback step 1 that a zero estimate gave)."""
+    n = 40
+    rows = np.repeat(np.arange(n), 2)
+    cols = np.stack([np.arange(n), (np.arange(n) + 1) % n], axis=1).ravel()
+    rng = np.random.default_rng(7)
+    lp = lpgen.from_pattern(n, n, rows, cols, np.tile([1.0, -1.0], n), rng, sense_probs=(1.0, 0.0, 0.0),
+                            var_probs=(1.0, 0.0, 0.0))
+    o = oracle.Options(mode="plain", alpha=0.0, phi=0)
+    P = oracle.scale_problem(lp, o)
+    assert np.all(P.A @ np.ones(n) == 0.0)
+    S0 = oracle.initial_state(P, o)
+    with lpop.Problem(lp, **gpu_options(o)) as p:
+        _, _, sc = p.scaling()
+    assert sc["norm_est"] > 1.0
+    assert sc["eta0"] == pytest.approx(S0.eta, rel=1e-12)
+
+
 def test_alpha_zero_keeps_identity_preconditioners():
     lp = lpgen.mixed_small(4)
     o = oracle.Options(alpha=0.0, phi=1)

@@ -440,6 +440,30 @@ def test_power_iteration_matches_svd():
     assert est == pytest.approx(np.linalg.norm(A.toarray(), 2), rel=1e-8)
 
 
+def _cycle_differences(n, seed=0):
+    """Rows w_i (x_i - x_{i+1 mod n}) with weights w_i ~ U(0.5, 2): every row
+    sums to zero, so the all-ones direction is in the null space."""
+    w = np.random.default_rng(seed).uniform(0.5, 2.0, size=n)
+    rows = np.repeat(np.arange(n), 2)
+    cols = np.stack([np.arange(n), (np.arange(n) + 1) % n], axis=1).ravel()
+    vals = np.stack([w, -w], axis=1).ravel()
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+def test_splitmix_signs_follow_the_published_generator():
+    g = load_golden("splitmix64.json")
+    want = [-1.0 if int(h, 16) >> 63 else 1.0 for h in g["outputs"]]
+    np.testing.assert_array_equal(oracle.pdhg.splitmix_signs(len(want)), want)
+
+
+def test_power_iteration_restarts_when_rows_sum_to_zero():
+    A = _cycle_differences(40)
+    assert np.all(np.asarray(A.sum(axis=1)).ravel() == 0.0)
+    assert np.all(A @ np.ones(40) == 0.0)
+    est = oracle.power_spectral_norm(A, 200)
+    assert est == pytest.approx(np.linalg.norm(A.toarray(), 2), rel=1e-8)
+
+
 def test_scaling_preserves_the_optimum():
     """The rescaled LP (mapped back) has the same optimum: HiGHS on both."""
     lp = lpgen.mixed_small(6, m=25, n=50)

@@ -54,3 +54,27 @@ def test_noalloc_power_norm_matches_lp_create():
         lpop.lp_power_norm_noalloc(lp.m, 1 << 20, *ptrs, iters=10, stream=stream)
     assert ei.value.code == lpop.LP_ERR_INVALID_ARG
     assert "scratch" in lpop.lp_last_error(None)
+
+
+def test_noalloc_power_norm_restarts_when_rows_sum_to_zero():
+    """Rows w_i (x_i - x_{i+1}) sum to zero, so the all-ones start direction is
+    in the null space of A; the entry point starts again from the SplitMix64
+    sign direction (as lp_create does) and finds the SVD norm."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lpbuild.build()
+    n = 40
+    w = np.random.default_rng(0).uniform(0.5, 2.0, size=n)
+    rows = np.repeat(np.arange(n), 2)
+    cols = np.stack([np.arange(n), (np.arange(n) + 1) % n], axis=1).ravel()
+    A = sp.csr_matrix((np.stack([w, -w], axis=1).ravel(), (rows, cols)), shape=(n, n))
+    a = _device_csr(torch, A)
+    at = _device_csr(torch, A.T)
+    ptrs = [t.data_ptr() for t in a] + [t.data_ptr() for t in at]
+    stream = torch.cuda.current_stream().cuda_stream
+    ref = np.linalg.norm(A.toarray(), 2)
+    for call in range(2):
+        est = lpop.lp_power_norm_noalloc(n, n, *ptrs, iters=200, stream=stream)
+        assert est == pytest.approx(ref, rel=1e-8), f"call {call}: {est!r} vs {ref!r}"
+
