@@ -266,6 +266,7 @@ def kernel_bytes(m, n, nnz, vb=8):
 # smaller instance of the same workload is scaled by the algorithmic bytes
 # (the units processed).  Re-take a capture whenever the kernel changes.
 NCU_TRAFFIC = {
+    ("transport", "dual", "double"): (9_050_880, 9_850_000, "profiles/transport_dual_step_full.md"),
     ("powerlaw", "primal", "double"): (66_398_976, 70_898_060, "profiles/powerlaw_primal_step_full.md (scale 0.1)"),
     ("powerlaw", "dual", "double"): (49_504_768, 53_098_060, "profiles/powerlaw_dual_step_full.md (scale 0.1)"),
     ("powerlaw", "primal", "float"): (38_588_928, 42_332_040,
