@@ -35,13 +35,18 @@ int widen_factor(long long rows, long long target_threads) {
   return f;
 }
 
-// Run fn(begin, end) over [0, count) split into contiguous pieces, on up to 8
-// host threads when the work (count by default; e.g. the entries of the
-// rows when a range is rows) is large.
+// Host threads for the layout's parallel phases: every hardware thread, up to 32.
+int layout_threads() {
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::min<unsigned>(hw == 0 ? 1u : hw, 32u);
+}
+
+// Run fn(begin, end) over [0, count) split into contiguous pieces, on the
+// layout's host threads when the work (count by default; e.g. the entries of
+// the rows when a range is rows) is large.
 template <class Fn>
 void parallel_ranges(long long count, Fn fn, long long work = -1) {
-  const unsigned hw = std::thread::hardware_concurrency();
-  int t = (int)std::min<unsigned>(hw == 0 ? 1u : hw, 8u);
+  int t = layout_threads();
   if ((work < 0 ? count : work) < (1 << 16)) t = 1;
   if (t <= 1) {
     fn(0LL, count);
@@ -236,8 +241,7 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
       std::vector<double> cv;
       std::vector<int64_t> len;
     };
-    const unsigned hw = std::thread::hardware_concurrency();
-    const int T = nnz < (1 << 16) ? 1 : (int)std::min<unsigned>(hw == 0 ? 1u : hw, 8u);
+    const int T = nnz < (1 << 16) ? 1 : layout_threads();
     std::vector<Part> parts(T);
     for (int t = 0; t < T; ++t) {
       parts[t].r0 = (long long)m * t / T;
@@ -304,7 +308,10 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
   out.nnz = nz;
   {
     auto columns = [&]() {
-      for (long long k = 0; k < nz; ++k) clen[ci[k]]++;
+      // column lengths: ranges of entries on the layout's threads, relaxed atomic increments
+      parallel_ranges(nz, [&](long long b, long long e) {
+        for (long long k = b; k < e; ++k) __atomic_fetch_add(&clen[ci[k]], 1LL, __ATOMIC_RELAXED);
+      });
       out.pcol = bin_permutation(clen, wAt, lAt, target_threads);
       out.binsAt = make_bins(wAt, lAt);
     };
@@ -357,9 +364,8 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
   out.At_ci.resize(nz);
   out.At_v.resize(nz);
   {
-    const unsigned hw = std::thread::hardware_concurrency();
-    int T = nz < (1 << 17) ? 1 : (int)std::min<unsigned>(hw == 0 ? 1u : hw, 8u);
-    while (T > 1 && (long long)T * n > (32LL << 20)) --T;  // bound the count table
+    int T = nz < (1 << 17) ? 1 : layout_threads();
+    while (T > 1 && (long long)T * n > (64LL << 20)) --T;  // bound the count table (256 MB)
     std::vector<int> fill((size_t)T * n);
     parallel_ranges_n(T, [&](int t) {
       int* f = fill.data() + (size_t)t * n;
