@@ -843,7 +843,9 @@ def serve_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 products/updates, f64 reductions and refinement",
         "data": "synthetic",
         "config": {"workload": f"{count} power-law LPs, nnz log-uniform [1e3, {args.serve_max_nnz:g}], n = nnz/6, "
-                               "m = 0.4 n, Poisson arrivals at load x (1 / mean one-at-a-time FP64 service time)",
+                               "m = 0.4 n, the large power-law recipe with column degrees capped at m/4 (its cap of "
+                               "1e5 exceeds m at these sizes), Poisson arrivals at load x (1 / mean one-at-a-time "
+                               "FP64 service time)",
                    "tol": TOL, "attempt_cap": cap, "loads": list(args.serve_loads),
                    "solo_nnz": args.serve_solo_nnz, "handoff_attempts": args.batch_handoff,
                    "note": ("power-law LPs above ~1e5 nonzeros need far more than 1e5 attempts to reach 1e-4, so "
