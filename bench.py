@@ -413,9 +413,10 @@ def end_to_end(lpop, lp, opts, tol, iter_limit, steps=3):
         t_total += time.perf_counter() - t0
         iters += st["iterations"]
     m, n, nnz = lp.m, lp.n, lp.nnz
-    # what lp_create copies to the device: CSR of A and of A^T (both built on the host:
-    # int32 row pointers and columns, float64 values), b, c, lb, ub and the senses
-    h2d = 4 * (m + 1) + 4 * (n + 1) + 24 * nnz + 8 * m + 3 * 8 * n + m
+    # what lp_create copies to the device: the caller's CSR of A (int64 row pointers,
+    # int32 columns, float64 values; the bin-ordered copies of A and A^T are built
+    # there), b, c, lb, ub and the senses
+    h2d = 8 * (m + 1) + 12 * nnz + 8 * m + 3 * 8 * n + m
     chunks = math.ceil(st["iterations"] / 64) + 1
     d2h = 8 * (m + n) + 4 * chunks
     return {"value": iters / t_total, "unit": "PDHG iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

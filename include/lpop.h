@@ -163,6 +163,11 @@ void lp_options_default(lp_options* opt);
  *   out           receives the handle on success, NULL on failure
  * Errors: LP_ERR_INVALID_ARG, LP_ERR_INVALID_INPUT (data checked on the host
  * before any device work), LP_ERR_CUDA, LP_ERR_OOM.
+ * The arrays are copied to the device once (rows with repeated entries or out
+ * of column order are first merged on the host); the bin-ordered copies of A
+ * and A^T are built there, with scratch taken from the problem's block of
+ * lp_memory_bytes() bytes (or, where it does not fit, from short-lived
+ * allocations of the same kind, freed before the call returns).
  * The call returns after the preprocessing has finished on the device.
  */
 int lp_create(int32_t m, int32_t n, int64_t nnz,

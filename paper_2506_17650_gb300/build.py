@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblpop.so")
 
-SOURCES = ["api.cu", "kernels_iter.cu", "kernels_check.cu", "kernels_setup.cu", "host_layout.cpp", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "kernels_iter.cu", "kernels_check.cu", "kernels_setup.cu", "host_layout.cpp", "device_layout.cu",
+           "noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,7 +1,8 @@
 // C ABI of the library (declared in include/lpop.h).
 //
-// lp_create validates on the host, builds the bin-ordered CSR copies of A and
-// A^T, uploads them and runs the preprocessing kernels.  lp_solve drives the
+// lp_create validates on the host, copies the caller's arrays to the device
+// once, builds the bin-ordered CSR copies of A and A^T there and runs the
+// preprocessing kernels.  lp_solve drives the
 // device-resident iteration: one check period (check_every step attempts and
 // the KKT check) is captured once as a CUDA graph and replayed; the host only
 // reads one status word per period.
@@ -16,6 +17,7 @@
 
 #include "../../include/lpop.h"
 #include "common.cuh"
+#include "device_layout.hpp"
 #include "host_layout.hpp"
 
 using namespace lpop;
@@ -358,19 +360,24 @@ int alloc_vecs(lp_problem* p, Vecs<V>& v, int m, int n, bool values) {
     TRY(dalloc(p, &v.Av, (size_t)p->d.nnz));
     TRY(dalloc(p, &v.Atv, (size_t)p->d.nnz));
   }
+  // (vectors already allocated, like the FP64 b, c, l and u the layout build fills, are kept)
   V** vm[] = {&v.b, &v.y[0], &v.y[1], &v.ax[0], &v.ax[1], &v.ybar[0], &v.ybar[1],
               &v.S, &v.invS, &v.GS, &v.p, &v.y_last, &v.ax_avg};
-  for (V** q : vm) TRY(dalloc(p, q, m));
+  for (V** q : vm)
+    if (!*q) TRY(dalloc(p, q, m));
   V** vn[] = {&v.c, &v.l, &v.u, &v.x[0], &v.x[1], &v.xbar[0], &v.xbar[1], &v.T, &v.invT, &v.GT, &v.q, &v.x_last};
-  for (V** q : vn) TRY(dalloc(p, q, n));
+  for (V** q : vn)
+    if (!*q) TRY(dalloc(p, q, n));
   return LP_OK;
 }
 
-int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* c, const double* lb,
-           const double* ub, const char* sense) {
+// Device buffers and the layout: the CSR copies of A and A^T and the vectors
+// in bin order are built on the device from the caller's (valid, canonical)
+// arrays, with scratch taken from the arena and given back afterwards.
+int upload(lp_problem* p, int m, int n, long long nz, const int64_t* row_ptr, const int32_t* col_idx,
+           const double* val, const double* b, const double* c, const double* lb, const double* ub,
+           const char* sense) {
   Dev& d = p->d;
-  const int m = lay.m, n = lay.n;
-  const long long nz = lay.nnz;
   d.m = m;
   d.n = n;
   TRY(dalloc(p, &d.A_rp, m + 1));
@@ -382,6 +389,38 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
   d.nnz = nz;
   d.f64.Av = d.A_v;
   d.f64.Atv = d.At_v;
+  TRY(dalloc(p, &d.f64.b, m));
+  TRY(dalloc(p, &d.sense, m));
+  TRY(dalloc(p, &d.f64.c, n));
+  TRY(dalloc(p, &d.f64.l, n));
+  TRY(dalloc(p, &d.f64.u, n));
+  LayoutInfo lay;
+  {
+    const size_t mark_used = p->arena_used, mark_allocs = p->allocs.size(), mark_ext = p->ext_allocs.size();
+    const ScratchAlloc scratch = [p](void** ptr, size_t bytes) {
+      char* q = nullptr;
+      const int rc = dalloc(p, &q, bytes);
+      *ptr = q;
+      return rc;
+    };
+    const LayoutArrays arr{d.A_rp, d.A_ci, d.A_v, d.At_rp, d.At_ci, d.At_v};
+    const LayoutVectors vecs{b, c, lb, ub, sense, d.f64.b, d.f64.c, d.f64.l, d.f64.u, d.sense};
+    std::string msg;
+    // FP64 rows take one lane up to kSellMaxLen entries whatever the matrix size (widen 1):
+    // extra lanes cost FP64 shuffle adds, which outweigh the added parallelism on GB300
+    const int rc = build_layout_device(m, n, nz, row_ptr, col_idx, val, 1, 1, arr, &vecs, lay, scratch, p->stream, msg);
+    // the scratch is dead once the build has returned: give it back
+    cudaStreamSynchronize(p->stream);
+    for (size_t k = mark_allocs; k < p->allocs.size(); ++k) cudaFree(p->allocs[k]);
+    p->allocs.resize(mark_allocs);
+    for (size_t k = mark_ext; k < p->ext_allocs.size(); ++k)
+      p->opt.device_free(p->ext_allocs[k].first, p->ext_allocs[k].second, p->opt.alloc_ctx);
+    p->ext_allocs.resize(mark_ext);
+    p->arena_used = mark_used;
+    if (rc != LP_OK) return set_err(p, rc, "layout build: " + msg);
+  }
+  p->prow = std::move(lay.prow);
+  p->pcol = std::move(lay.pcol);
   TRY(dalloc(p, &d.dr, m));
   TRY(dalloc(p, &d.dc, n));
   TRY(dalloc(p, &d.inv_dr, m));
@@ -389,7 +428,6 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
   TRY(alloc_vecs(p, d.f64, m, n, false));
   if (p->mixed) TRY(alloc_vecs(p, d.f32, m, n, true));
   TRY(dalloc(p, &d.work2, (size_t)(m > n ? m : n) + 1));
-  TRY(dalloc(p, &d.sense, m));
   TRY(dalloc(p, &d.work, (size_t)m + n + 2048));
   TRY(dalloc(p, &d.st, 1));
   {
@@ -409,9 +447,9 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
   // work are then cut into segments, which adds units
   const int cap_d = sms * per_sm_d, cap_p = sms * per_sm_p;
   auto grid_of = [](int units, int cap) { return units < 1 ? 1 : (units < cap ? units : cap); };
-  std::vector<int> segA = segment_long_rows(d.binsA, lay.A_rp, segment_length(nz, grid_of(d.binsA.nunits, cap_d)));
+  std::vector<int> segA = segment_long_rows(d.binsA, lay.A_head, segment_length(nz, grid_of(d.binsA.nunits, cap_d)));
   std::vector<int> segAt =
-      segment_long_rows(d.binsAt, lay.At_rp, segment_length(nz, grid_of(d.binsAt.nunits, cap_p)));
+      segment_long_rows(d.binsAt, lay.At_head, segment_length(nz, grid_of(d.binsAt.nunits, cap_p)));
   d.gridA = grid_of(d.binsA.nunits, cap_d);
   d.gridAt = grid_of(d.binsAt.nunits, cap_p);
   d.gridA32 = grid_of(d.binsA.nunits, sms * per_sm_d32);
@@ -428,13 +466,8 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
     CK(cudaMemsetAsync(bt.ticket, 0, sizeof(unsigned int) * bt.seg_rows, p->stream));
     bt.seg_unit = su;
   }
-  for (int which = 0; which < 2; ++which) {
-    const std::vector<int>& rp = which ? lay.At_rp : lay.A_rp;
-    const int rows = which ? n : m;
-    int r = 0;
-    while (r < rows && rp[r + 1] - rp[r] > 32) ++r;
-    p->split[which] = r;
-  }
+  p->split[0] = lay.split[0];
+  p->split[1] = lay.split[1];
   for (int which = 0; which < 2; ++which) {  // sliced copies: filled on the device once the values are final
     const long long ns = sliced_entries(which ? d.binsAt : d.binsA);
     p->sell_n[which] = ns;
@@ -451,37 +484,6 @@ int upload(lp_problem* p, const HostLayout& lay, const double* b, const double* 
   TRY(dalloc(p, &d.partials2, (size_t)maxg * kMaxPartials));
   d.A = Csr{d.A_rp, d.A_ci, d.A_v};
   d.At = Csr{d.At_rp, d.At_ci, d.At_v};
-
-  cudaStream_t s = p->stream;
-  CK(cudaMemcpyAsync(d.A_rp, lay.A_rp.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(d.At_rp, lay.At_rp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
-  if (nz > 0) {
-    CK(cudaMemcpyAsync(d.A_ci, lay.A_ci.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d.A_v, lay.A_v.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d.At_ci, lay.At_ci.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d.At_v, lay.At_v.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, s));
-  }
-  // vectors in bin order
-  std::vector<double> tm(m), tn(n);
-  std::vector<uint8_t> ts(m);
-  for (int i = 0; i < m; ++i) tm[i] = b[lay.prow[i]];
-  if (m > 0) CK(cudaMemcpyAsync(d.f64.b, tm.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s));
-  for (int i = 0; i < m; ++i) {
-    const char c0 = sense[lay.prow[i]];
-    ts[i] = c0 == 'E' ? kEq : (c0 == 'L' ? kLe : kGe);
-  }
-  if (m > 0) CK(cudaMemcpyAsync(d.sense, ts.data(), m, cudaMemcpyHostToDevice, s));
-  std::vector<double> tl(n), tu(n);
-  for (int j = 0; j < n; ++j) {
-    const int o = lay.pcol[j];
-    tn[j] = c[o];
-    tl[j] = lb[o];
-    tu[j] = ub[o];
-  }
-  CK(cudaMemcpyAsync(d.f64.c, tn.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(d.f64.l, tl.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(d.f64.u, tu.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
-  CK(cudaStreamSynchronize(s));  // the host buffers end with this function
   return LP_OK;
 }
 
@@ -699,16 +701,23 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
       return set_err(nullptr, LP_ERR_INVALID_INPUT,
                      "bounds of variable " + std::to_string(j) + " are invalid (need lb <= ub, lb < inf, ub > -inf)");
   }
-  // FP64 rows take one lane up to kSellMaxLen entries whatever the matrix size:
-  // extra lanes cost FP64 shuffle adds, which outweigh the added parallelism on GB300
-  HostLayout lay;
-  int rc = build_layout(m, n, nnz, row_ptr, col_idx, val, lay, msg, 0);
+  bool canonical = true;
+  int rc = validate_csr(m, n, nnz, row_ptr, col_idx, val, canonical, msg);
   if (rc != LP_OK) return set_err(nullptr, rc, msg);
+  // rows out of column order or with repeated entries: sorted and merged (summed) here first
+  std::vector<int64_t> rp_m;
+  std::vector<int> ci_m;
+  std::vector<double> cv_m;
+  if (!canonical) merge_rows(m, row_ptr, col_idx, val, rp_m, ci_m, cv_m);
+  const int64_t* rp = canonical ? row_ptr : rp_m.data();
+  const int32_t* ci = canonical ? col_idx : ci_m.data();
+  const double* cv = canonical ? val : cv_m.data();
+  const long long nz = canonical ? (long long)nnz : (long long)ci_m.size();
 
   p = new lp_problem();
   p->opt = o;
   p->mixed = o.precision == LP_PREC_MIXED;
-  p->nnz = lay.nnz;
+  p->nnz = nz;
   auto fail = [&](int code) {
     g_last_error = p->err;
     release(p);
@@ -736,8 +745,6 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
     set_err(p, LP_ERR_OOM, "pinned host allocation failed");
     return fail(LP_ERR_OOM);
   }
-  p->prow = lay.prow;
-  p->pcol = lay.pcol;
   p->prm.m = m;
   p->prm.n = n;
   p->prm.mode = o.mode;
@@ -752,7 +759,7 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
   p->prm.refine_stall = o.refine_stall;
   {
     int64_t bytes = 0;
-    if (lp_memory_bytes(m, n, lay.nnz, &o, &bytes) == LP_OK && bytes > 0) {
+    if (lp_memory_bytes(m, n, nz, &o, &bytes) == LP_OK && bytes > 0) {
       void* a = nullptr;
       if (o.device_alloc) {
         a = o.device_alloc((size_t)bytes, o.alloc_ctx);
@@ -775,7 +782,7 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
       }
     }
   }
-  if ((rc = upload(p, lay, b, c, lb, ub, sense)) != LP_OK) return fail(rc);
+  if ((rc = upload(p, m, n, nz, rp, ci, cv, b, c, lb, ub, sense)) != LP_OK) return fail(rc);
   if ((rc = preprocess(p)) != LP_OK) return fail(rc);
   if ((rc = create_events(p)) != LP_OK) return fail(rc);
   if ((rc = init_state(p)) != LP_OK) return fail(rc);

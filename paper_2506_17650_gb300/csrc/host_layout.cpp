@@ -12,29 +12,6 @@ namespace lpop {
 
 namespace {
 
-// Work order of the bins: whole-block rows first (they are the longest, so
-// they start early), then 32, 16, ... 1 lanes.
-int bin_rank(int width) {
-  switch (width) {
-    case 0: return 0;
-    case 32: return 1;
-    case 16: return 2;
-    case 8: return 3;
-    case 4: return 4;
-    case 2: return 5;
-    default: return 6;
-  }
-}
-
-constexpr long long kBlockRowThreshold = 2048;  // rows longer than this get a whole block
-
-// Power of two >= the ratio target / rows, capped at 8 (1 when rows fill the GPU).
-int widen_factor(long long rows, long long target_threads) {
-  int f = 1;
-  while (f < 8 && (long long)f * rows < target_threads) f <<= 1;
-  return f;
-}
-
 // Host threads for the layout's parallel phases: every hardware thread, up to 32.
 int layout_threads() {
   const unsigned hw = std::thread::hardware_concurrency();
@@ -83,7 +60,6 @@ std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<
   // a warp's rows get similar lengths and the heaviest units come first.
   // Counting sort on (rank, length) for rows up to kCountMax entries; the few
   // longer rows (all in the whole-block bin) are sorted directly and go first.
-  constexpr int kCountMax = 4096;
   std::vector<int> longer;
   std::vector<long long> start(7 * (kCountMax + 1) + 1, 0);
   auto key = [&](int r) { return bin_rank(width[r]) * (kCountMax + 1) + (kCountMax - (int)len[r]); };
@@ -109,32 +85,35 @@ std::vector<int> bin_permutation(const std::vector<long long>& len, std::vector<
 
 }  // namespace
 
-// Lanes per row.  Rows of up to kSellMaxLen entries get one lane each, from
-// the sliced copy (every load of a warp contiguous): on GB300 the FP64 pipe
-// limits these kernels, and one lane per row needs no shuffle adds to combine
-// lane sums and runs the row's epilogue on every lane (with W lanes per row
-// the epilogue's FP64 instructions run on one lane in W).  Longer rows split
-// over 4..32 lanes.
-int width_for_length(long long len, int widen) {
-  int w;
-  if (len <= kSellMaxLen) w = 1;
-  else if (len <= 64) w = 4;
-  else if (len <= 256) w = 16;
-  else if (len <= kBlockRowThreshold) w = 32;
-  else return 0;
-  // a short row gains nothing from more lanes than entries
-  int cap = 1;
-  while (cap < len && cap < 32) cap <<= 1;
-  const int wide = widen < cap ? widen : cap;
-  return w > wide ? w : wide;
+int widen_factor(long long rows, long long target_threads) {
+  int f = 1;
+  while (f < 8 && (long long)f * rows < target_threads) f <<= 1;
+  return f;
 }
 
-BinTable make_bins(const std::vector<int>& widths_sorted, const std::vector<int>& lengths_sorted) {
+BinTable bins_from_runs(const std::vector<BinRun>& runs) {
   BinTable t{};
   t.nbins = 0;
   t.nunits = 0;
-  const int rows = (int)widths_sorted.size();
   long long sell = 0;
+  for (const BinRun& x : runs) {
+    Bin& b = t.bin[t.nbins++];
+    b.row_begin = x.row_begin;
+    b.row_end = x.row_end;
+    b.width = x.width;
+    b.unit_begin = t.nunits;
+    b.len = x.width == kSell ? x.len : 0;
+    b.base = x.width == kSell ? sell : 0;
+    if (x.width == kSell) sell += (long long)(x.row_end - x.row_begin + 31) / 32 * 32 * x.len;
+    const int per = rows_per_unit(b);
+    t.nunits += (x.row_end - x.row_begin + per - 1) / per;
+  }
+  return t;
+}
+
+BinTable make_bins(const std::vector<int>& widths_sorted, const std::vector<int>& lengths_sorted) {
+  std::vector<BinRun> runs;
+  const int rows = (int)widths_sorted.size();
   int r = 0;
   while (r < rows) {
     const int w = widths_sorted[r];
@@ -142,21 +121,12 @@ BinTable make_bins(const std::vector<int>& widths_sorted, const std::vector<int>
     const bool sliced = w == 1 && !lengths_sorted.empty();
     int e = r;
     while (e < rows && widths_sorted[e] == w && (!sliced || lengths_sorted[e] == lengths_sorted[r])) ++e;
-    // at most kSellMaxLen + 1 sliced lengths and six other classes: within kMaxBins
-    static_assert(kSellMaxLen + 1 + 6 + 1 <= kMaxBins, "bin table too small");
-    Bin& b = t.bin[t.nbins++];
-    b.row_begin = r;
-    b.row_end = e;
-    b.width = sliced ? kSell : w;
-    b.unit_begin = t.nunits;
-    b.len = sliced ? lengths_sorted[r] : 0;
-    b.base = sliced ? sell : 0;
-    if (sliced) sell += (long long)(e - r + 31) / 32 * 32 * b.len;
-    const int per = rows_per_unit(b);
-    t.nunits += (e - r + per - 1) / per;
+    runs.push_back(BinRun{r, e, sliced ? kSell : w, sliced ? lengths_sorted[r] : 0});
     r = e;
   }
-  return t;
+  // at most kSellMaxLen + 1 sliced lengths and six other classes: within kMaxBins
+  static_assert(kSellMaxLen + 1 + 6 + 1 <= kMaxBins, "bin table too small");
+  return bins_from_runs(runs);
 }
 
 long long sliced_entries(const BinTable& bt) {
@@ -168,8 +138,8 @@ long long sliced_entries(const BinTable& bt) {
   return total;
 }
 
-int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
-                 const double* val, HostLayout& out, std::string& err, long long target_threads) {
+int validate_csr(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* val, bool& canonical, std::string& err) {
   if (m < 0 || n < 1 || nnz < 0) {
     err = "need m >= 0, n >= 1 and nnz >= 0";
     return LP_ERR_INVALID_ARG;
@@ -195,7 +165,7 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
   // entries (on host threads, by ranges of rows): the first one with a column
   // out of range or a value that is not finite, and whether every row is in
   // strictly increasing column order
-  bool canonical = true;
+  canonical = true;
   {
     std::mutex mu;
     int64_t bad = nnz;
@@ -222,79 +192,85 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
       return LP_ERR_INVALID_INPUT;
     }
   }
+  return LP_OK;
+}
 
+void merge_rows(int32_t m, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                std::vector<int64_t>& rp, std::vector<int>& ci, std::vector<double>& cv) {
+  const int64_t nnz = row_ptr[m];
+  rp.assign(m + 1, 0);
+  struct Part {
+    long long r0 = 0, r1 = 0;
+    std::vector<int> ci;
+    std::vector<double> cv;
+    std::vector<int64_t> len;
+  };
+  const int T = nnz < (1 << 16) ? 1 : layout_threads();
+  std::vector<Part> parts(T);
+  for (int t = 0; t < T; ++t) {
+    parts[t].r0 = (long long)m * t / T;
+    parts[t].r1 = (long long)m * (t + 1) / T;
+  }
+  auto work = [&](Part& P) {
+    std::vector<std::pair<int, double>> row;
+    P.ci.reserve(row_ptr[P.r1] - row_ptr[P.r0]);
+    P.cv.reserve(row_ptr[P.r1] - row_ptr[P.r0]);
+    P.len.reserve(P.r1 - P.r0);
+    for (long long i = P.r0; i < P.r1; ++i) {
+      const size_t before = P.ci.size();
+      bool sorted = true;
+      for (int64_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) sorted = sorted && col_idx[k - 1] < col_idx[k];
+      if (sorted) {  // the common case: copy as is
+        P.ci.insert(P.ci.end(), col_idx + row_ptr[i], col_idx + row_ptr[i + 1]);
+        P.cv.insert(P.cv.end(), val + row_ptr[i], val + row_ptr[i + 1]);
+      } else {
+        row.clear();
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) row.emplace_back(col_idx[k], val[k]);
+        std::stable_sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (size_t t = 0; t < row.size();) {
+          const int c = row[t].first;
+          double sum = row[t].second;
+          size_t e = t + 1;
+          while (e < row.size() && row[e].first == c) sum += row[e++].second;
+          P.ci.push_back(c);
+          P.cv.push_back(sum);
+          t = e;
+        }
+      }
+      P.len.push_back((int64_t)(P.ci.size() - before));
+    }
+  };
+  if (T == 1) {
+    work(parts[0]);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < T; ++t) pool.emplace_back([&, t]() { work(parts[t]); });
+    for (auto& th : pool) th.join();
+  }
+  long long total = 0;
+  for (const Part& P : parts) total += (long long)P.ci.size();
+  ci.resize(total);
+  cv.resize(total);
+  long long off = 0;
+  for (const Part& P : parts) {
+    std::copy(P.ci.begin(), P.ci.end(), ci.begin() + off);
+    std::copy(P.cv.begin(), P.cv.end(), cv.begin() + off);
+    for (long long i = P.r0; i < P.r1; ++i) rp[i + 1] = rp[i] + P.len[i - P.r0];
+    off += (long long)P.ci.size();
+  }
+}
+
+int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* val, HostLayout& out, std::string& err, long long target_threads) {
+  bool canonical = true;
+  if (const int rc = validate_csr(m, n, nnz, row_ptr, col_idx, val, canonical, err)) return rc;
   // rows in strictly increasing column order (the common case) are used in
   // place; otherwise each row is sorted by column and repeated entries are
-  // merged (summed), row ranges on host threads, each into its own buffers,
-  // then concatenated
+  // merged (summed)
   std::vector<int64_t> rp_m;
   std::vector<int> ci_m;
   std::vector<double> cv_m;
-  if (!canonical) {
-    std::vector<int64_t>& rp = rp_m;
-    std::vector<int>& ci = ci_m;
-    std::vector<double>& cv = cv_m;
-    rp.assign(m + 1, 0);
-    struct Part {
-      long long r0 = 0, r1 = 0;
-      std::vector<int> ci;
-      std::vector<double> cv;
-      std::vector<int64_t> len;
-    };
-    const int T = nnz < (1 << 16) ? 1 : layout_threads();
-    std::vector<Part> parts(T);
-    for (int t = 0; t < T; ++t) {
-      parts[t].r0 = (long long)m * t / T;
-      parts[t].r1 = (long long)m * (t + 1) / T;
-    }
-    auto work = [&](Part& P) {
-      std::vector<std::pair<int, double>> row;
-      P.ci.reserve(row_ptr[P.r1] - row_ptr[P.r0]);
-      P.cv.reserve(row_ptr[P.r1] - row_ptr[P.r0]);
-      P.len.reserve(P.r1 - P.r0);
-      for (long long i = P.r0; i < P.r1; ++i) {
-        const size_t before = P.ci.size();
-        bool sorted = true;
-        for (int64_t k = row_ptr[i] + 1; k < row_ptr[i + 1]; ++k) sorted = sorted && col_idx[k - 1] < col_idx[k];
-        if (sorted) {  // the common case: copy as is
-          P.ci.insert(P.ci.end(), col_idx + row_ptr[i], col_idx + row_ptr[i + 1]);
-          P.cv.insert(P.cv.end(), val + row_ptr[i], val + row_ptr[i + 1]);
-        } else {
-          row.clear();
-          for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) row.emplace_back(col_idx[k], val[k]);
-          std::stable_sort(row.begin(), row.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
-          for (size_t t = 0; t < row.size();) {
-            const int c = row[t].first;
-            double sum = row[t].second;
-            size_t e = t + 1;
-            while (e < row.size() && row[e].first == c) sum += row[e++].second;
-            P.ci.push_back(c);
-            P.cv.push_back(sum);
-            t = e;
-          }
-        }
-        P.len.push_back((int64_t)(P.ci.size() - before));
-      }
-    };
-    if (T == 1) {
-      work(parts[0]);
-    } else {
-      std::vector<std::thread> pool;
-      for (int t = 0; t < T; ++t) pool.emplace_back([&, t]() { work(parts[t]); });
-      for (auto& th : pool) th.join();
-    }
-    long long total = 0;
-    for (const Part& P : parts) total += (long long)P.ci.size();
-    ci.resize(total);
-    cv.resize(total);
-    long long off = 0;
-    for (const Part& P : parts) {
-      std::copy(P.ci.begin(), P.ci.end(), ci.begin() + off);
-      std::copy(P.cv.begin(), P.cv.end(), cv.begin() + off);
-      for (long long i = P.r0; i < P.r1; ++i) rp[i + 1] = rp[i] + P.len[i - P.r0];
-      off += (long long)P.ci.size();
-    }
-  }
+  if (!canonical) merge_rows(m, row_ptr, col_idx, val, rp_m, ci_m, cv_m);
   const int64_t* rp = canonical ? row_ptr : rp_m.data();
   const int32_t* ci = canonical ? col_idx : ci_m.data();
   const double* cv = canonical ? val : cv_m.data();

@@ -21,15 +21,24 @@ struct HostLayout {
   BinTable binsA{}, binsAt{};
 };
 
-// Lanes per row for a row of length len: 1, 2, 4, ..., 32, or 0 (a block per
-// row).  `widen` (a power of two >= 1) asks for up to that many lanes on short
-// rows when a matrix has too few rows to occupy the GPU with one lane each.
-int width_for_length(long long len, int widen = 1);
+// Check a caller's CSR matrix: sizes and pointers, row_ptr (0 first, nnz
+// last, non-decreasing), then every entry (column in range, finite value),
+// on host threads.  Returns 0, or a negative lp_err code with a message
+// naming the first offending index in err; sets canonical when every row is
+// in strictly increasing column order.
+int validate_csr(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* val, bool& canonical, std::string& err);
 
-// Validate the CSR input and build the layout.  Returns 0 on success, or a
-// negative lp_err code with a message in err.  target_threads: threads that
-// fill the GPU (SMs x resident threads); matrices with fewer rows get wider
-// row groups.
+// The rows of a valid CSR matrix sorted by column with repeated entries
+// summed (rows already in strictly increasing order are copied as they are),
+// on host threads.
+void merge_rows(int32_t m, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                std::vector<int64_t>& rp, std::vector<int>& ci, std::vector<double>& cv);
+
+// Validate the CSR input and build the layout on the host.  Returns 0 on
+// success, or a negative lp_err code with a message in err.  target_threads:
+// threads that fill the GPU (SMs x resident threads); matrices with fewer
+// rows get wider row groups.
 int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                  const double* val, HostLayout& out, std::string& err, long long target_threads = 0);
 
@@ -37,6 +46,19 @@ int build_layout(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
 // rows first within a width).  One-lane rows form kSell bins of one exact
 // length each (no kSell bins when lengths_sorted is empty).
 BinTable make_bins(const std::vector<int>& widths_sorted, const std::vector<int>& lengths_sorted);
+
+// One maximal run of rows of one width (and, for kSell, of one length).
+struct BinRun {
+  int row_begin, row_end, width, len;
+};
+
+// Bin table from the runs of a matrix in bin order (width kSell for sliced
+// runs): unit numbering and sliced-copy offsets.
+BinTable bins_from_runs(const std::vector<BinRun>& runs);
+
+// Widen factor of build_layout for a matrix of `rows` rows: a power of two
+// >= target_threads / rows, capped at 8 (1 when the rows fill the GPU).
+int widen_factor(long long rows, long long target_threads);
 
 // Entries of the sliced copy of a table's kSell bins (padding included); the
 // copy itself is filled on the device.

@@ -3,6 +3,12 @@
 
 #include <stdint.h>
 
+#if defined(__CUDACC__)
+#define LPOP_HD __host__ __device__
+#else
+#define LPOP_HD
+#endif
+
 namespace lpop {
 
 constexpr int kBlock = 256;      // threads per block of every row kernel
@@ -41,10 +47,57 @@ struct Bin {
 };
 
 // Rows per work unit of a bin.
-inline int rows_per_unit(const Bin& b) {
+LPOP_HD inline int rows_per_unit(const Bin& b) {
   if (b.width == 0 || b.width == kSegmented) return 1;
   if (b.width == kSell) return b.len <= kPairMaxLen ? 2 * kBlock : kBlock;
   return kBlock / b.width;
+}
+
+constexpr long long kBlockRowThreshold = 2048;  // rows longer than this get a whole block
+constexpr int kCountMax = 4096;                 // rows up to this long are ordered by a counting key
+
+// Lanes per row for a row of length len: 1 up to kSellMaxLen entries (one
+// lane per row needs no shuffle adds to combine lane sums and runs the row's
+// epilogue on every lane: on GB300 the FP64 pipe limits these kernels), 4, 16
+// or 32 for longer rows, 0 (a block per row) beyond kBlockRowThreshold.
+// `widen` (a power of two >= 1) asks for up to that many lanes on short rows
+// when a matrix has too few rows to occupy the GPU with one lane each.
+LPOP_HD inline int width_for_length(long long len, int widen = 1) {
+  int w;
+  if (len <= kSellMaxLen) w = 1;
+  else if (len <= 64) w = 4;
+  else if (len <= 256) w = 16;
+  else if (len <= kBlockRowThreshold) w = 32;
+  else return 0;
+  // a short row gains nothing from more lanes than entries
+  int cap = 1;
+  while (cap < len && cap < 32) cap <<= 1;
+  const int wide = widen < cap ? widen : cap;
+  return w > wide ? w : wide;
+}
+
+// Work order of the row classes: whole-block rows first (they are the
+// longest, so they start early), then 32, 16, ... 1 lanes.
+LPOP_HD inline int bin_rank(int width) {
+  switch (width) {
+    case 0: return 0;
+    case 32: return 1;
+    case 16: return 2;
+    case 8: return 3;
+    case 4: return 4;
+    case 2: return 5;
+    default: return 6;
+  }
+}
+
+// Position key of a row in the bin order of a matrix whose longest row has
+// lmax entries: ascending keys put the rows longer than kCountMax first
+// (longest first), then class by class in work order, longest first within a
+// class.  Sorting the rows stably by this key gives the bin order.
+LPOP_HD inline unsigned order_key(long long len, int widen, long long lmax) {
+  const long long base = (lmax > kCountMax ? lmax : kCountMax) - kCountMax;
+  if (len > kCountMax) return (unsigned)(base + kCountMax - len);
+  return (unsigned)(base + (long long)bin_rank(width_for_length(len, widen)) * (kCountMax + 1) + (kCountMax - len));
 }
 
 struct BinTable {
