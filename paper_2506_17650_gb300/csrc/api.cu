@@ -23,7 +23,8 @@
 using namespace lpop;
 
 namespace lpop {
-void launch_mul_into(double* out, const double* a, const double* f, int n, cudaStream_t s);
+void launch_scatter_perm(double* out, const double* a, const double* f, const int* perm, int n, cudaStream_t s);
+void launch_gather_perm(double* out, const double* a, const int* perm, int n, cudaStream_t s);
 void row_kernel_blocks_per_sm(int* primal, int* dual, int* primal32, int* dual32);
 }  // namespace lpop
 
@@ -42,6 +43,8 @@ struct lp_problem {
   Dev d{};
   Params prm{};
   std::vector<int> prow, pcol;
+  int* d_prow = nullptr;  // the same permutations on the device
+  int* d_pcol = nullptr;
   double eta0 = 1.0, omega0 = 1.0, norm_est = 0.0, amax = 0.0;
   long long nnz = 0;
   bool initial_check_done = false;
@@ -74,7 +77,7 @@ struct lp_problem {
   // indices and values, filled on the device once the preprocessed values
   // are final
   long long sell_n[2] = {0, 0};
-  int split[2] = {0, 0};  // first row of A / A^T with at most 32 entries (rows are sorted longest first)
+  RuizSplit ruiz[2] = {};  // how the Ruiz kernels cut the rows of A / A^T
   int* sell_ci[2] = {nullptr, nullptr};
   double* sell_v[2] = {nullptr, nullptr};
   float* sell_v32[2] = {nullptr, nullptr};
@@ -260,9 +263,9 @@ int preprocess(lp_problem* p) {
   double* red = d.work + m + n;  // reduction scratch [1 + 1024]
   launch_fill(d.dr, 1.0, m, s);
   launch_fill(d.dc, 1.0, n, s);
-  auto apply = [&]() { launch_ruiz_apply(d, p->split[0], p->split[1], fr, fc, s); };
+  auto apply = [&]() { launch_ruiz_apply(d, p->ruiz[0], p->ruiz[1], fr, fc, s); };
   for (int r = 0; r < p->opt.ruiz_iters; ++r) {
-    launch_ruiz_norms(d, p->split[0], p->split[1], fr, fc, s);
+    launch_ruiz_norms(d, p->ruiz[0], p->ruiz[1], fr, fc, s);
     apply();
   }
   if (p->opt.mode == LP_MODE_PDLP) {
@@ -394,6 +397,8 @@ int upload(lp_problem* p, int m, int n, long long nz, const int64_t* row_ptr, co
   TRY(dalloc(p, &d.f64.c, n));
   TRY(dalloc(p, &d.f64.l, n));
   TRY(dalloc(p, &d.f64.u, n));
+  TRY(dalloc(p, &p->d_prow, m));
+  TRY(dalloc(p, &p->d_pcol, n));
   LayoutInfo lay;
   {
     const size_t mark_used = p->arena_used, mark_allocs = p->allocs.size(), mark_ext = p->ext_allocs.size();
@@ -403,7 +408,7 @@ int upload(lp_problem* p, int m, int n, long long nz, const int64_t* row_ptr, co
       *ptr = q;
       return rc;
     };
-    const LayoutArrays arr{d.A_rp, d.A_ci, d.A_v, d.At_rp, d.At_ci, d.At_v};
+    const LayoutArrays arr{d.A_rp, d.A_ci, d.A_v, d.At_rp, d.At_ci, d.At_v, p->d_prow, p->d_pcol};
     const LayoutVectors vecs{b, c, lb, ub, sense, d.f64.b, d.f64.c, d.f64.l, d.f64.u, d.sense};
     std::string msg;
     // FP64 rows take one lane up to kSellMaxLen entries whatever the matrix size (widen 1):
@@ -466,8 +471,23 @@ int upload(lp_problem* p, int m, int n, long long nz, const int64_t* row_ptr, co
     CK(cudaMemsetAsync(bt.ticket, 0, sizeof(unsigned int) * bt.seg_rows, p->stream));
     bt.seg_unit = su;
   }
-  p->split[0] = lay.split[0];
-  p->split[1] = lay.split[1];
+  for (int which = 0; which < 2; ++which) {  // Ruiz units: whole-block rows in chunks, then warp and thread rows
+    const std::vector<int>& head = which ? lay.At_head : lay.A_head;
+    RuizSplit& rs = p->ruiz[which];
+    rs.split = lay.split[which];
+    rs.nlong = head.empty() ? 0 : (int)head.size() - 1;
+    rs.nchunks = 0;
+    rs.chunk_pre = nullptr;
+    if (rs.nlong == 0) continue;
+    std::vector<int> pre((size_t)rs.nlong + 1, 0);
+    for (int r = 0; r < rs.nlong; ++r) pre[r + 1] = pre[r] + (head[r + 1] - head[r] + kRuizChunk - 1) / kRuizChunk;
+    rs.nchunks = pre[rs.nlong];
+    int* dp = nullptr;
+    TRY(dalloc(p, &dp, pre.size()));
+    CK(cudaMemcpyAsync(dp, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    rs.chunk_pre = dp;
+  }
   for (int which = 0; which < 2; ++which) {  // sliced copies: filled on the device once the values are final
     const long long ns = sliced_entries(which ? d.binsAt : d.binsA);
     p->sell_n[which] = ns;
@@ -541,8 +561,7 @@ int collect_times(lp_problem* p) {
   return LP_OK;
 }
 
-int download_vec(lp_problem* p, const double* dsrc, const double* dscale, int len, const std::vector<int>& perm,
-                 double* out);
+int download_vec(lp_problem* p, const double* dsrc, const double* dscale, int len, const int* dperm, double* out);
 
 // The current phase's copy of a vector as FP64 on the device (FP32 vectors are widened into work2).
 const double* phase_vec(lp_problem* p, const double* v64, const float* v32, int len) {
@@ -551,27 +570,25 @@ const double* phase_vec(lp_problem* p, const double* v64, const float* v32, int 
   return p->d.work2;
 }
 
-int download_vec(lp_problem* p, const double* dsrc, const double* dscale, int len, const std::vector<int>& perm,
-                 double* out) {
+// A device vector in the caller's order (out[perm[i]] = src[i], times
+// scale[i] when given), put together on the device and copied into out.
+int download_vec(lp_problem* p, const double* dsrc, const double* dscale, int len, const int* dperm, double* out) {
   if (!out || len == 0) return LP_OK;
   double* tmp = p->d.work;  // [m + n + 2048] >= len
-  if (dscale) {
-    launch_mul_into(tmp, dsrc, dscale, len, p->stream);
-    CK(cudaGetLastError());
-    dsrc = tmp;
-  }
-  std::vector<double> h(len);
-  CK(cudaMemcpyAsync(h.data(), dsrc, sizeof(double) * len, cudaMemcpyDeviceToHost, p->stream));
+  launch_scatter_perm(tmp, dsrc, dscale, dperm, len, p->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, tmp, sizeof(double) * len, cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
-  for (int i = 0; i < len; ++i) out[perm[i]] = h[i];
   return LP_OK;
 }
 
-int upload_vec(lp_problem* p, double* ddst, const double* host, int len, const std::vector<int>& perm) {
+// The caller's vector into a device vector in bin order (dst[i] = host[perm[i]]).
+int upload_vec(lp_problem* p, double* ddst, const double* host, int len, const int* dperm) {
   if (len == 0) return LP_OK;
-  std::vector<double> h(len);
-  for (int i = 0; i < len; ++i) h[i] = host[perm[i]];
-  CK(cudaMemcpyAsync(ddst, h.data(), sizeof(double) * len, cudaMemcpyHostToDevice, p->stream));
+  double* tmp = p->d.work;  // [m + n + 2048] >= len
+  CK(cudaMemcpyAsync(tmp, host, sizeof(double) * len, cudaMemcpyHostToDevice, p->stream));
+  launch_gather_perm(ddst, tmp, dperm, len, p->stream);
+  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(p->stream));
   return LP_OK;
 }
@@ -589,13 +606,13 @@ int get_state_impl(lp_problem* p, double* vn, double* vm, double* scal) {
     const double* s64[5] = {d.f64.x[c], d.f64.xbar[c], d.f64.T, d.f64.GT, d.f64.x_last};
     const float* s32[5] = {d.f32.x[c], d.f32.xbar[c], d.f32.T, d.f32.GT, d.f32.x_last};
     for (int k = 0; k < 5; ++k)
-      TRY(download_vec(p, phase_vec(p, s64[k], s32[k], n), nullptr, n, p->pcol, vn + (size_t)k * n));
+      TRY(download_vec(p, phase_vec(p, s64[k], s32[k], n), nullptr, n, p->d_pcol, vn + (size_t)k * n));
   }
   if (vm) {
     const double* s64[6] = {d.f64.y[c], d.f64.ybar[c], d.f64.ax[c], d.f64.S, d.f64.GS, d.f64.y_last};
     const float* s32[6] = {d.f32.y[c], d.f32.ybar[c], d.f32.ax[c], d.f32.S, d.f32.GS, d.f32.y_last};
     for (int k = 0; k < 6; ++k)
-      TRY(download_vec(p, phase_vec(p, s64[k], s32[k], m), nullptr, m, p->prow, vm + (size_t)k * m));
+      TRY(download_vec(p, phase_vec(p, s64[k], s32[k], m), nullptr, m, p->d_prow, vm + (size_t)k * m));
   }
   if (scal) {
     const double v[16] = {hs.eta, hs.omega, hs.wsum, hs.gp_norm, hs.gd_norm, hs.klast_p2, hs.klast_d2,
@@ -618,9 +635,9 @@ int set_state_impl(lp_problem* p, const double* vn, const double* vm, const doub
   const int n = p->d.n, m = p->d.m, c = hs.cur;
   const Dev& d = p->d;
   double* dn[5] = {d.f64.x[c], d.f64.xbar[c], d.f64.T, d.f64.GT, d.f64.x_last};
-  for (int k = 0; k < 5; ++k) TRY(upload_vec(p, dn[k], vn + (size_t)k * n, n, p->pcol));
+  for (int k = 0; k < 5; ++k) TRY(upload_vec(p, dn[k], vn + (size_t)k * n, n, p->d_pcol));
   double* dm[6] = {d.f64.y[c], d.f64.ybar[c], d.f64.ax[c], d.f64.S, d.f64.GS, d.f64.y_last};
-  for (int k = 0; k < 6; ++k) TRY(upload_vec(p, dm[k], vm + (size_t)k * m, m, p->prow));
+  for (int k = 0; k < 6; ++k) TRY(upload_vec(p, dm[k], vm + (size_t)k * m, m, p->d_prow));
   hs.eta = scal[0];
   hs.omega = scal[1];
   hs.inv_omega = 1.0 / hs.omega;
@@ -690,16 +707,23 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
   if (m < 0 || n < 1) return set_err(nullptr, LP_ERR_INVALID_ARG, "need m >= 0 and n >= 1");
   if ((m > 0 && (!b || !sense)) || !c || !lb || !ub)
     return set_err(nullptr, LP_ERR_INVALID_ARG, "b, c, lb, ub and sense must not be NULL");
-  for (int i = 0; i < m; ++i) {
-    if (!std::isfinite(b[i])) return set_err(nullptr, LP_ERR_INVALID_INPUT, "b[" + std::to_string(i) + "] is not finite");
-    if (sense[i] != 'E' && sense[i] != 'L' && sense[i] != 'G')
-      return set_err(nullptr, LP_ERR_INVALID_INPUT, "sense[" + std::to_string(i) + "] must be 'E', 'L' or 'G'");
+  // the first offending row, then the first offending column (on host threads)
+  auto bad_row = [&](long long i) {
+    return !std::isfinite(b[i]) || (sense[i] != 'E' && sense[i] != 'L' && sense[i] != 'G');
+  };
+  auto bad_bounds = [&](long long j) {
+    return std::isnan(lb[j]) || std::isnan(ub[j]) || lb[j] == INFINITY || ub[j] == -INFINITY || lb[j] > ub[j];
+  };
+  const long long i0 = first_bad_index(m, bad_row);
+  if (i0 < m) {
+    if (!std::isfinite(b[i0])) return set_err(nullptr, LP_ERR_INVALID_INPUT, "b[" + std::to_string(i0) + "] is not finite");
+    return set_err(nullptr, LP_ERR_INVALID_INPUT, "sense[" + std::to_string(i0) + "] must be 'E', 'L' or 'G'");
   }
-  for (int j = 0; j < n; ++j) {
-    if (!std::isfinite(c[j])) return set_err(nullptr, LP_ERR_INVALID_INPUT, "c[" + std::to_string(j) + "] is not finite");
-    if (std::isnan(lb[j]) || std::isnan(ub[j]) || lb[j] == INFINITY || ub[j] == -INFINITY || lb[j] > ub[j])
-      return set_err(nullptr, LP_ERR_INVALID_INPUT,
-                     "bounds of variable " + std::to_string(j) + " are invalid (need lb <= ub, lb < inf, ub > -inf)");
+  const long long j0 = first_bad_index(n, [&](long long j) { return !std::isfinite(c[j]) || bad_bounds(j); });
+  if (j0 < n) {
+    if (!std::isfinite(c[j0])) return set_err(nullptr, LP_ERR_INVALID_INPUT, "c[" + std::to_string(j0) + "] is not finite");
+    return set_err(nullptr, LP_ERR_INVALID_INPUT,
+                   "bounds of variable " + std::to_string(j0) + " are invalid (need lb <= ub, lb < inf, ub > -inf)");
   }
   bool canonical = true;
   int rc = validate_csr(m, n, nnz, row_ptr, col_idx, val, canonical, msg);
@@ -1011,8 +1035,8 @@ int lp_result(lp_problem* p, double* x, double* y, lp_stats* st) {
   DevState hs;
   CK(cudaMemcpyAsync(&hs, p->d.st, sizeof(hs), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
-  if (x) TRY(download_vec(p, phase_vec(p, p->d.f64.x[hs.cur], p->d.f32.x[hs.cur], p->d.n), p->d.dc, p->d.n, p->pcol, x));
-  if (y) TRY(download_vec(p, phase_vec(p, p->d.f64.y[hs.cur], p->d.f32.y[hs.cur], p->d.m), p->d.dr, p->d.m, p->prow, y));
+  if (x) TRY(download_vec(p, phase_vec(p, p->d.f64.x[hs.cur], p->d.f32.x[hs.cur], p->d.n), p->d.dc, p->d.n, p->d_pcol, x));
+  if (y) TRY(download_vec(p, phase_vec(p, p->d.f64.y[hs.cur], p->d.f32.y[hs.cur], p->d.m), p->d.dr, p->d.m, p->d_prow, y));
   if (st) {
     std::memset(st, 0, sizeof(*st));
     st->pobj = hs.pobj;
@@ -1041,10 +1065,10 @@ int lp_get_iterate(lp_problem* p, double* x, double* y, double* T, double* Sigma
   CK(cudaStreamSynchronize(p->stream));
   const Dev& d = p->d;
   const int c = hs.cur;
-  if (x) TRY(download_vec(p, phase_vec(p, d.f64.x[c], d.f32.x[c], d.n), nullptr, d.n, p->pcol, x));
-  if (y) TRY(download_vec(p, phase_vec(p, d.f64.y[c], d.f32.y[c], d.m), nullptr, d.m, p->prow, y));
-  if (T) TRY(download_vec(p, phase_vec(p, d.f64.T, d.f32.T, d.n), nullptr, d.n, p->pcol, T));
-  if (Sigma) TRY(download_vec(p, phase_vec(p, d.f64.S, d.f32.S, d.m), nullptr, d.m, p->prow, Sigma));
+  if (x) TRY(download_vec(p, phase_vec(p, d.f64.x[c], d.f32.x[c], d.n), nullptr, d.n, p->d_pcol, x));
+  if (y) TRY(download_vec(p, phase_vec(p, d.f64.y[c], d.f32.y[c], d.m), nullptr, d.m, p->d_prow, y));
+  if (T) TRY(download_vec(p, phase_vec(p, d.f64.T, d.f32.T, d.n), nullptr, d.n, p->d_pcol, T));
+  if (Sigma) TRY(download_vec(p, phase_vec(p, d.f64.S, d.f32.S, d.m), nullptr, d.m, p->d_prow, Sigma));
   if (scal) {
     scal[0] = hs.eta;
     scal[1] = hs.omega;
@@ -1061,8 +1085,8 @@ int lp_get_iterate(lp_problem* p, double* x, double* y, double* T, double* Sigma
 int lp_get_scaling(lp_problem* p, double* dr, double* dc, double* scal) {
   if (!p) return set_err(nullptr, LP_ERR_INVALID_ARG, "problem handle is NULL");
   TRY(select_device(p));
-  TRY(download_vec(p, p->d.dr, nullptr, p->d.m, p->prow, dr));
-  TRY(download_vec(p, p->d.dc, nullptr, p->d.n, p->pcol, dc));
+  TRY(download_vec(p, p->d.dr, nullptr, p->d.m, p->d_prow, dr));
+  TRY(download_vec(p, p->d.dc, nullptr, p->d.n, p->d_pcol, dc));
   if (scal) {
     scal[0] = p->eta0;
     scal[1] = p->omega0;
@@ -1118,6 +1142,8 @@ int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, in
   const long long S = nnz / 4096 + 1;
   t += 2 * (r(8LL * 2 * S) + r(16LL * 2 * S) + r(4LL * S));
   t += 2 * r(8LL * kMaxPartials * (4096 + S));  // per-block records (upper bound of the grid) and row slots
+  t += 2 * r(4LL * (nnz / 2048 + 2));             // chunk tables of the whole-block rows (Ruiz)
+  t += r(4LL * m) + r(4LL * n);                    // the row and column permutations
   // sliced copies of the rows of up to kSellMaxLen entries (at most nnz entries plus the
   // padding of the last slices of kSellMaxLen + 1 bins)
   const long long SE = nnz + (kSellMaxLen + 1LL) * 31 * kSellMaxLen;
@@ -1144,16 +1170,30 @@ void lp_destroy(lp_problem* p) { release(p); }
 namespace lpop {
 
 namespace {
-__global__ void mul_into_kernel(double* out, const double* a, const double* f, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[i] * f[i];
+// out[perm[i]] = a[i] (times f[i] when f is given)
+__global__ void scatter_perm_kernel(double* out, const double* a, const double* f, const int* perm, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[perm[i]] = f ? a[i] * f[i] : a[i];
+}
+
+// out[i] = a[perm[i]]
+__global__ void gather_perm_kernel(double* out, const double* a, const int* perm, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = a[perm[i]];
+}
+
+int perm_grid(int n) {
+  int g = (n + kBlock - 1) / kBlock;
+  if (g > 4096) g = 4096;
+  return g < 1 ? 1 : g;
 }
 }  // namespace
 
-void launch_mul_into(double* out, const double* a, const double* f, int n, cudaStream_t s) {
-  int g = (n + kBlock - 1) / kBlock;
-  if (g > 1024) g = 1024;
-  if (g < 1) g = 1;
-  mul_into_kernel<<<g, kBlock, 0, s>>>(out, a, f, n);
+void launch_scatter_perm(double* out, const double* a, const double* f, const int* perm, int n, cudaStream_t s) {
+  scatter_perm_kernel<<<perm_grid(n), kBlock, 0, s>>>(out, a, f, perm, n);
+}
+
+void launch_gather_perm(double* out, const double* a, const int* perm, int n, cudaStream_t s) {
+  gather_perm_kernel<<<perm_grid(n), kBlock, 0, s>>>(out, a, perm, n);
 }
 
 }  // namespace lpop

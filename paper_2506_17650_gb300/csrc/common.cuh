@@ -470,8 +470,20 @@ void launch_fill(double* v, double val, long long n, cudaStream_t s);
 //   norms: fr = row infinity norms of A, fc = those of A^T (columns of A);
 //   apply: f <- f > 0 ? 1/sqrt(f) : 1 for fr and fc, dr *= fr, dc *= fc, and
 //          every entry a_ij <- (a_ij fr_i) fc_j in both copies.
-void launch_ruiz_norms(const Dev& d, int split_a, int split_at, double* fr, double* fc, cudaStream_t s);
-void launch_ruiz_apply(const Dev& d, int split_a, int split_at, double* fr, double* fc, cudaStream_t s);
+// How the Ruiz kernels cut the rows of one matrix: rows [0, nlong) (the
+// whole-block rows) in chunks of kRuizChunk entries, one warp each
+// (chunk_pre: device prefix of their chunk counts, nlong + 1 entries, nchunks
+// in all), rows [nlong, split) a warp each, rows [split, rows) (at most 32
+// entries) a thread each.
+constexpr int kRuizChunk = 1024;
+struct RuizSplit {
+  int split;
+  int nlong;
+  int nchunks;
+  const int* chunk_pre;
+};
+void launch_ruiz_norms(const Dev& d, const RuizSplit& a, const RuizSplit& at, double* fr, double* fc, cudaStream_t s);
+void launch_ruiz_apply(const Dev& d, const RuizSplit& a, const RuizSplit& at, double* fr, double* fc, cudaStream_t s);
 void launch_row_powsum(const Csr& M, int rows, double beta, int square_root, double* out, cudaStream_t s);
 void launch_scale_problem_vectors(const Dev& d, cudaStream_t s);
 void launch_init_vectors(const Dev& d, cudaStream_t s);

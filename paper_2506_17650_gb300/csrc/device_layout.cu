@@ -479,11 +479,13 @@ int build_layout_device(int32_t m, int32_t n, int64_t nnz, const int64_t* row_pt
   TRYD(get(&rlen, m));
   TRYD(get(&clen, n));
   TRYD(get(&icol, n));
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < 2; ++k) {  // the sorted permutations end in idxA[1] / idxT[1]
     TRYD(get(&keyA[k], m));
-    TRYD(get(&idxA[k], m));
     TRYD(get(&keyT[k], n));
-    TRYD(get(&idxT[k], n));
+    if (k == 1 && out.prow) idxA[1] = out.prow;
+    else TRYD(get(&idxA[k], m));
+    if (k == 1 && out.pcol) idxT[1] = out.pcol;
+    else TRYD(get(&idxT[k], n));
   }
   TRYD(get(&Kp, nz));
   TRYD(get(&Kq, nz));

@@ -17,7 +17,9 @@
 namespace lpop {
 
 // Device arrays of a layout, allocated by the caller: the permuted CSR of A
-// (m + 1 row pointers, nnz entries) and of A^T (n + 1, nnz).
+// (m + 1 row pointers, nnz entries) and of A^T (n + 1, nnz), and optionally
+// (null: not kept) the permutations themselves (permuted index -> caller's
+// index, m and n entries).
 struct LayoutArrays {
   int* A_rp;
   int* A_ci;
@@ -25,6 +27,8 @@ struct LayoutArrays {
   int* At_rp;
   int* At_ci;
   double* At_v;
+  int* prow;
+  int* pcol;
 };
 
 // Optional: the caller's b, c, lb, ub and senses (host) and their device

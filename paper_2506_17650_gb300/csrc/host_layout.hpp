@@ -5,6 +5,7 @@
 
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -20,6 +21,10 @@ struct HostLayout {
   std::vector<double> A_v, At_v;
   BinTable binsA{}, binsAt{};
 };
+
+// Smallest i in [0, count) with bad(i), or count if there is none; on the
+// layout's host threads when count is large.
+long long first_bad_index(long long count, const std::function<bool(long long)>& bad);
 
 // Check a caller's CSR matrix: sizes and pointers, row_ptr (0 first, nnz
 // last, non-decreasing), then every entry (column in range, finite value),

@@ -37,35 +37,76 @@ __global__ void row_powsum_kernel(Csr M, int rows, double beta, int square_root,
   }
 }
 
-// Rows of one matrix in a Ruiz round: rows [0, split) -- the longer ones,
-// rows being sorted longest first -- take a warp each, rows [split, rows) (at
-// most 32 entries) a thread each.  Unit w of the matrix is warp row w for
-// w < split, else the 32 thread rows split + 32 (w - split) + lane.
+// Rows of one matrix in a Ruiz round (rows sorted longest first): the
+// whole-block rows [0, nlong) in chunks of kRuizChunk entries, rows
+// [nlong, split) a warp each, rows [split, rows) (at most 32 entries) a
+// thread each.  Units: chunk units [0, nchunks), then one per warp row, then
+// one per 32 thread rows.
 struct RuizRows {
   const int* rp;
   const int* ci;
   double* v;
   int rows;
-  int split;
-  __device__ __forceinline__ long long units() const { return split + (rows - split + 31) / 32; }
+  RuizSplit sp;
+  __host__ __device__ __forceinline__ long long units() const {
+    return sp.nchunks + (sp.split - sp.nlong) + (rows - sp.split + 31) / 32;
+  }
+  // unit w -> (row, first entry, end entry, step) for this lane; false if the lane has no row
+  __device__ __forceinline__ bool range(long long w, int lane, long long& r, long long& k0, long long& k1,
+                                        int& step) const {
+    r = k0 = k1 = 0;
+    step = 1;
+    if (w < sp.nchunks) {  // the row whose chunks include w: the last r with chunk_pre[r] <= w
+      int lo = 0, hi = sp.nlong;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sp.chunk_pre[mid] <= w) lo = mid;
+        else hi = mid;
+      }
+      r = lo;
+      const long long c0 = rp[r] + (w - sp.chunk_pre[lo]) * (long long)kRuizChunk;
+      k0 = c0 + lane;
+      k1 = min((long long)rp[r + 1], c0 + kRuizChunk);
+      step = 32;
+      return true;
+    }
+    w -= sp.nchunks;
+    if (w < sp.split - sp.nlong) {
+      r = sp.nlong + w;
+      k0 = rp[r] + lane;
+      k1 = rp[r + 1];
+      step = 32;
+      return true;
+    }
+    r = sp.split + (w - (sp.split - sp.nlong)) * 32 + lane;
+    if (r >= rows) return false;
+    k0 = rp[r];
+    k1 = rp[r + 1];
+    return true;
+  }
 };
 
-// out[r] = max_k |v_k| for the rows of unit w (max is exact: the result
-// does not depend on the order).
+// out[r] = max_k |v_k| for the rows of unit w (max is exact: the result does
+// not depend on the order, so the chunks of a row combine by atomic max on
+// the bit patterns of their non-negative maxima, into an out[r] zeroed
+// before the launch).
 __device__ __forceinline__ void absmax_unit(const RuizRows& R, long long w, int lane, double* out) {
-  if (w < R.split) {
-    const int r = (int)w;
-    double mx = 0.0;
-    for (int k = R.rp[r] + lane; k < R.rp[r + 1]; k += 32) mx = fmax(mx, fabs(R.v[k]));
+  long long r, k0, k1;
+  int step;
+  const bool has = R.range(w, lane, r, k0, k1, step);
+  double mx = 0.0;
+  if (has)
+    for (long long k = k0; k < k1; k += step) mx = fmax(mx, fabs(R.v[k]));
+  if (step == 32) {  // warp units (uniform across the warp)
     for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) out[r] = mx;
-  } else {
-    const long long r = R.split + (w - R.split) * 32 + lane;
-    if (r < R.rows) {
-      double mx = 0.0;
-      for (int k = R.rp[r]; k < R.rp[r + 1]; ++k) mx = fmax(mx, fabs(R.v[k]));
-      out[r] = mx;
+    if (lane == 0) {
+      if (w < R.sp.nchunks)
+        atomicMax(reinterpret_cast<unsigned long long*>(out + r), (unsigned long long)__double_as_longlong(mx));
+      else
+        out[r] = mx;
     }
+  } else if (has) {
+    out[r] = mx;
   }
 }
 
@@ -76,17 +117,7 @@ __device__ __forceinline__ void scale_unit(const RuizRows& R, long long w, int l
                                            const double* fcol, bool a_rows) {
   long long r, k0, k1;
   int step;
-  if (w < R.split) {
-    r = w;
-    k0 = R.rp[r] + lane;
-    step = 32;
-  } else {
-    r = R.split + (w - R.split) * 32 + lane;
-    if (r >= R.rows) return;
-    k0 = R.rp[r];
-    step = 1;
-  }
-  k1 = R.rp[r + 1];
+  if (!R.range(w, lane, r, k0, k1, step)) return;
   for (long long k = k0; k < k1; k += step) {
     const int c = R.ci[k];
     const long long i = a_rows ? r : c;
@@ -355,22 +386,24 @@ void launch_row_powsum(const Csr& M, int rows, double beta, int square_root, dou
 }
 
 namespace {
-RuizRows ruiz_rows(int* rp, int* ci, double* v, int rows, int split) { return RuizRows{rp, ci, v, rows, split}; }
-int ruiz_grid(const Dev& d, int split_a, int split_at) {
-  const long long units = split_a + (d.m - split_a + 31) / 32 + split_at + (d.n - split_at + 31) / 32;
+int ruiz_grid(const RuizRows& a, const RuizRows& at) {
+  const long long units = a.units() + at.units();
   return warp_grid_for(units);
 }
 }  // namespace
 
-void launch_ruiz_norms(const Dev& d, int split_a, int split_at, double* fr, double* fc, cudaStream_t s) {
-  ruiz_norms_kernel<<<ruiz_grid(d, split_a, split_at), kBlock, 0, s>>>(
-      ruiz_rows(d.A_rp, d.A_ci, d.A_v, d.m, split_a), ruiz_rows(d.At_rp, d.At_ci, d.At_v, d.n, split_at), fr, fc);
+void launch_ruiz_norms(const Dev& d, const RuizSplit& a, const RuizSplit& at, double* fr, double* fc, cudaStream_t s) {
+  const RuizRows A{d.A_rp, d.A_ci, d.A_v, d.m, a}, At{d.At_rp, d.At_ci, d.At_v, d.n, at};
+  // the chunked rows' maxima are combined by atomic max from zero
+  if (a.nlong > 0) cudaMemsetAsync(fr, 0, sizeof(double) * a.nlong, s);
+  if (at.nlong > 0) cudaMemsetAsync(fc, 0, sizeof(double) * at.nlong, s);
+  ruiz_norms_kernel<<<ruiz_grid(A, At), kBlock, 0, s>>>(A, At, fr, fc);
 }
 
-void launch_ruiz_apply(const Dev& d, int split_a, int split_at, double* fr, double* fc, cudaStream_t s) {
+void launch_ruiz_apply(const Dev& d, const RuizSplit& a, const RuizSplit& at, double* fr, double* fc, cudaStream_t s) {
+  const RuizRows A{d.A_rp, d.A_ci, d.A_v, d.m, a}, At{d.At_rp, d.At_ci, d.At_v, d.n, at};
   factor_mul_kernel<<<grid_for((long long)d.m + d.n), kBlock, 0, s>>>(fr, d.dr, d.m, fc, d.dc, d.n);
-  ruiz_scale_kernel<<<ruiz_grid(d, split_a, split_at), kBlock, 0, s>>>(
-      ruiz_rows(d.A_rp, d.A_ci, d.A_v, d.m, split_a), ruiz_rows(d.At_rp, d.At_ci, d.At_v, d.n, split_at), fr, fc);
+  ruiz_scale_kernel<<<ruiz_grid(A, At), kBlock, 0, s>>>(A, At, fr, fc);
 }
 
 void launch_scale_problem_vectors(const Dev& d, cudaStream_t s) {

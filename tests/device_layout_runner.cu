@@ -129,7 +129,8 @@ int main(int argc, char** argv) {
 
   std::vector<void*> owned;
   lpop::LayoutArrays arr{dev<int>((size_t)m + 1, owned), dev<int>(nz, owned), dev<double>(nz, owned),
-                         dev<int>((size_t)n + 1, owned), dev<int>(nz, owned), dev<double>(nz, owned)};
+                         dev<int>((size_t)n + 1, owned), dev<int>(nz, owned), dev<double>(nz, owned),
+                         dev<int>(m, owned), dev<int>(n, owned)};
   lpop::LayoutVectors vec{b.data(), c.data(), lb.data(), ub.data(), sense.data(),
                           dev<double>(m, owned), dev<double>(n, owned), dev<double>(n, owned),
                           dev<double>(n, owned), dev<uint8_t>(m, owned)};
@@ -175,6 +176,8 @@ int main(int argc, char** argv) {
   // beyond the host runner's format
   put<int>(o, info.split[0]);
   put<int>(o, info.split[1]);
+  put_vec(o, ok ? down(arr.prow, (size_t)m) : std::vector<int>());
+  put_vec(o, ok ? down(arr.pcol, (size_t)n) : std::vector<int>());
   put_vec(o, ok ? down(vec.d_b, (size_t)m) : std::vector<double>());
   put_vec(o, ok ? down(vec.d_sense, (size_t)m) : std::vector<uint8_t>());
   put_vec(o, ok ? down(vec.d_c, (size_t)n) : std::vector<double>());

@@ -8,8 +8,9 @@ permutations, both permuted CSR copies, the bin tables and the segmentation.
 Inputs: the generators' shapes (power-law columns longer than the counting
 range, whole-block and segmented rows included), shuffled rows with repeated
 entries, empty rows, no constraints, and the widened layouts.  The device
-runner also reports the first rows of at most 32 entries and the permuted
-copies of b, c, lb, ub and the senses, checked here against the host layout.
+runner also reports the first rows of at most 32 entries, the device copies
+of the permutations and the permuted copies of b, c, lb, ub and the senses,
+checked here against the host layout.
 """
 import os
 import shutil
@@ -71,8 +72,8 @@ def run_both(runners, tmp_path, m, n, rp, ci, v, target=0, seg_len=0):
     assert r.o == len(host)
     x = _Reader(dev)
     x.o = len(host)
-    extra = dict(split=(x.take("<i"), x.take("<i")), b=x.vec(np.float64), sense=x.vec(np.uint8),
-                 c=x.vec(np.float64), l=x.vec(np.float64), u=x.vec(np.float64))
+    extra = dict(split=(x.take("<i"), x.take("<i")), prow=x.vec(np.int32), pcol=x.vec(np.int32), b=x.vec(np.float64),
+                 sense=x.vec(np.uint8), c=x.vec(np.float64), l=x.vec(np.float64), u=x.vec(np.float64))
     return lay, extra
 
 
@@ -81,6 +82,7 @@ def check_extra(lay, extra, m, n):
         short = np.flatnonzero(np.diff(rp) <= 32)
         assert extra["split"][which] == (short[0] if len(short) else rows)
     i, j = lay["prow"], lay["pcol"]
+    assert np.array_equal(extra["prow"], i) and np.array_equal(extra["pcol"], j)  # the device copies kept
     assert np.array_equal(extra["b"], i + 0.5)
     assert np.array_equal(extra["sense"], i % 3)  # E, L, G -> 0, 1, 2
     assert np.array_equal(extra["c"], -1.0 - j)
