@@ -269,11 +269,11 @@ int preprocess(lp_problem* p) {
     apply();
   }
   if (p->opt.mode == LP_MODE_PDLP) {
-    launch_row_powsum(d.A, m, p->opt.pc_beta, 0, fr, s);
-    launch_row_powsum(d.At, n, 2.0 - p->opt.pc_beta, 0, fc, s);
+    launch_row_powsum(d.A, m, p->ruiz[0].nlong, p->ruiz[0].split, p->opt.pc_beta, 0, fr, s);
+    launch_row_powsum(d.At, n, p->ruiz[1].nlong, p->ruiz[1].split, 2.0 - p->opt.pc_beta, 0, fc, s);
   } else {
-    launch_row_powsum(d.A, m, 2.0, 1, fr, s);
-    launch_row_powsum(d.At, n, 2.0, 1, fc, s);
+    launch_row_powsum(d.A, m, p->ruiz[0].nlong, p->ruiz[0].split, 2.0, 1, fr, s);
+    launch_row_powsum(d.At, n, p->ruiz[1].nlong, p->ruiz[1].split, 2.0, 1, fc, s);
   }
   apply();
   CK(cudaGetLastError());

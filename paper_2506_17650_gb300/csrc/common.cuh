@@ -484,7 +484,10 @@ struct RuizSplit {
 };
 void launch_ruiz_norms(const Dev& d, const RuizSplit& a, const RuizSplit& at, double* fr, double* fc, cudaStream_t s);
 void launch_ruiz_apply(const Dev& d, const RuizSplit& a, const RuizSplit& at, double* fr, double* fc, cudaStream_t s);
-void launch_row_powsum(const Csr& M, int rows, double beta, int square_root, double* out, cudaStream_t s);
+// out[r] = sum over row r of |a|^beta (optionally its square root); rows [0, nlong) are the whole-block
+// rows, rows [split, rows) those of at most 32 entries
+void launch_row_powsum(const Csr& M, int rows, int nlong, int split, double beta, int square_root, double* out,
+                       cudaStream_t s);
 void launch_scale_problem_vectors(const Dev& d, cudaStream_t s);
 void launch_init_vectors(const Dev& d, cudaStream_t s);
 void launch_spmv_binned(const Csr& M, const BinTable& bt, int grid, const double* x, double* y, cudaStream_t s);

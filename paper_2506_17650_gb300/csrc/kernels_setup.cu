@@ -22,26 +22,62 @@ __global__ void fill_kernel(double* v, double val, long long n) {
     v[i] = val;
 }
 
-// one warp per row: out[r] = sum_k |v_k|^beta (beta == 1 and beta == 2 exact), optionally sqrt
-__global__ void row_powsum_kernel(Csr M, int rows, double beta, int square_root, double* out) {
+__device__ __forceinline__ double pow_term(double v, double beta) {
+  const double a = fabs(v);
+  return beta == 1.0 ? a : (beta == 2.0 ? a * a : (beta == 0.0 ? 1.0 : pow(a, beta)));
+}
+
+// out[r] = sum_k |v_k|^beta (beta == 1 and beta == 2 exact), optionally sqrt:
+// the whole-block rows [0, nlong) a block each (four strided partial sums
+// per thread, so that four loads are in flight, then the block's fixed
+// tree), rows [nlong, split) a warp each, the rows of at most 32 entries
+// [split, rows) eight lanes each (four rows per warp at a time); a lane's
+// terms are summed in order, then the lanes' sums by a butterfly.
+__global__ void row_powsum_kernel(Csr M, int rows, int nlong, int split, double beta, int square_root, double* out) {
+  __shared__ double smem[32];
+  for (int r = blockIdx.x; r < nlong; r += gridDim.x) {
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    const int k1 = M.rp[r + 1];
+    int k = M.rp[r] + threadIdx.x;
+    for (; k + 3 * kBlock < k1; k += 4 * kBlock) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s4[q] += pow_term(M.v[k + q * kBlock], beta);
+    }
+    if (k < k1) s4[0] += pow_term(M.v[k], beta);  // at most three left
+    if (k + kBlock < k1) s4[1] += pow_term(M.v[k + kBlock], beta);
+    if (k + 2 * kBlock < k1) s4[2] += pow_term(M.v[k + 2 * kBlock], beta);
+    double s[1] = {(s4[0] + s4[1]) + (s4[2] + s4[3])};
+    block_sum<1>(s, smem);
+    if (threadIdx.x == 0) out[r] = square_root ? sqrt(s[0]) : s[0];
+  }
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  for (int r = nlong + wid; r < split; r += warps) {
     double s = 0.0;
-    for (int k = M.rp[r] + lane; k < M.rp[r + 1]; k += 32) {
-      const double a = fabs(M.v[k]);
-      s += beta == 1.0 ? a : (beta == 2.0 ? a * a : (beta == 0.0 ? 1.0 : pow(a, beta)));
-    }
+#pragma unroll 4
+    for (int k = M.rp[r] + lane; k < M.rp[r + 1]; k += 32) s += pow_term(M.v[k], beta);
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) out[r] = square_root ? sqrt(s) : s;
+  }
+  for (long long r0 = split + 4LL * wid; r0 < rows; r0 += 4LL * warps) {
+    const long long r = r0 + (lane >> 3);
+    double s = 0.0;
+    if (r < rows) {
+#pragma unroll 4
+      for (int k = M.rp[r] + (lane & 7); k < M.rp[r + 1]; k += 8) s += pow_term(M.v[k], beta);
+    }
+    for (int off = 4; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((lane & 7) == 0 && r < rows) out[r] = square_root ? sqrt(s) : s;
   }
 }
 
 // Rows of one matrix in a Ruiz round (rows sorted longest first): the
 // whole-block rows [0, nlong) in chunks of kRuizChunk entries, rows
-// [nlong, split) a warp each, rows [split, rows) (at most 32 entries) a
-// thread each.  Units: chunk units [0, nchunks), then one per warp row, then
-// one per 32 thread rows.
+// [nlong, split) a warp each, rows [split, rows) (at most 32 entries) four
+// lanes each, so that a warp's loads cover eight runs of consecutive
+// entries.  Units (one per warp): chunk units [0, nchunks), then one per warp
+// row, then one per eight short rows.
 struct RuizRows {
   const int* rp;
   const int* ci;
@@ -49,7 +85,7 @@ struct RuizRows {
   int rows;
   RuizSplit sp;
   __host__ __device__ __forceinline__ long long units() const {
-    return sp.nchunks + (sp.split - sp.nlong) + (rows - sp.split + 31) / 32;
+    return sp.nchunks + (sp.split - sp.nlong) + (rows - sp.split + 7) / 8;
   }
   // unit w -> (row, first entry, end entry, step) for this lane; false if the lane has no row
   __device__ __forceinline__ bool range(long long w, int lane, long long& r, long long& k0, long long& k1,
@@ -78,9 +114,10 @@ struct RuizRows {
       step = 32;
       return true;
     }
-    r = sp.split + (w - (sp.split - sp.nlong)) * 32 + lane;
+    step = 4;
+    r = sp.split + (w - (sp.split - sp.nlong)) * 8 + (lane >> 2);
     if (r >= rows) return false;
-    k0 = rp[r];
+    k0 = rp[r] + (lane & 3);
     k1 = rp[r + 1];
     return true;
   }
@@ -95,17 +132,20 @@ __device__ __forceinline__ void absmax_unit(const RuizRows& R, long long w, int 
   int step;
   const bool has = R.range(w, lane, r, k0, k1, step);
   double mx = 0.0;
-  if (has)
+  if (has) {
+#pragma unroll 4
     for (long long k = k0; k < k1; k += step) mx = fmax(mx, fabs(R.v[k]));
-  if (step == 32) {  // warp units (uniform across the warp)
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  }
+  // step is uniform across the warp: 32 for chunk and warp rows, 4 for eight short rows
+  for (int off = step == 32 ? 16 : 2; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if (step == 32) {
     if (lane == 0) {
       if (w < R.sp.nchunks)
         atomicMax(reinterpret_cast<unsigned long long*>(out + r), (unsigned long long)__double_as_longlong(mx));
       else
         out[r] = mx;
     }
-  } else if (has) {
+  } else if (has && (lane & 3) == 0) {
     out[r] = mx;
   }
 }
@@ -118,6 +158,7 @@ __device__ __forceinline__ void scale_unit(const RuizRows& R, long long w, int l
   long long r, k0, k1;
   int step;
   if (!R.range(w, lane, r, k0, k1, step)) return;
+#pragma unroll 4
   for (long long k = k0; k < k1; k += step) {
     const int c = R.ci[k];
     const long long i = a_rows ? r : c;
@@ -381,8 +422,11 @@ void launch_fill(double* v, double val, long long n, cudaStream_t s) {
 }
 
 
-void launch_row_powsum(const Csr& M, int rows, double beta, int square_root, double* out, cudaStream_t s) {
-  if (rows > 0) row_powsum_kernel<<<warp_grid_for(rows), kBlock, 0, s>>>(M, rows, beta, square_root, out);
+void launch_row_powsum(const Csr& M, int rows, int nlong, int split, double beta, int square_root, double* out,
+                       cudaStream_t s) {
+  if (rows > 0)
+    row_powsum_kernel<<<warp_grid_for(nlong + (split - nlong) + (rows - split + 3) / 4), kBlock, 0, s>>>(
+        M, rows, nlong, split, beta, square_root, out);
 }
 
 namespace {
