@@ -372,7 +372,7 @@ def roofline(kind, m, n, nnz, kt_ms, kt_n, clk, label):
     fp64_peak = SMS * FP64_LANES_PER_SM_CLK * sm_clk / 1e9
     fp64_achieved = dom_ops / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
     traffic = NCU_TRAFFIC.get((kind, dom, label))
-    return {
+    out = {
         "bound": "hbm",
         "kernel": f"{dom}_step_kernel<{label}> (fused sparse product + update)",
         "achieved": achieved,
@@ -388,10 +388,12 @@ def roofline(kind, m, n, nnz, kt_ms, kt_n, clk, label):
         "other_kernel_bytes_per_launch": db if dom == "primal" else pb,
         "attempt_bytes": pb + db,
         "samples": int(kt_n[0]),
-        "fp64_alu": {"achieved": fp64_achieved, "peak": fp64_peak, "unit": "G FP64 inst/s",
-                     "frac": fp64_achieved / fp64_peak if fp64_achieved else None, "ops_per_launch": dom_ops,
-                     "peak_from": f"{SMS} SMs x {FP64_LANES_PER_SM_CLK} FP64 lanes/cycle x median SM clock"},
     }
+    if label == "double":  # the FP32 kernels' products and updates are FP32; FP64 only in sums and scalars
+        out["fp64_alu"] = {"achieved": fp64_achieved, "peak": fp64_peak, "unit": "G FP64 inst/s",
+                           "frac": fp64_achieved / fp64_peak if fp64_achieved else None, "ops_per_launch": dom_ops,
+                           "peak_from": f"{SMS} SMs x {FP64_LANES_PER_SM_CLK} FP64 lanes/cycle x median SM clock"}
+    return out
 
 
 def end_to_end(lpop, lp, opts, tol, iter_limit, steps=3):
