@@ -69,7 +69,8 @@ int widen_factor(long long rows, long long target_threads);
 // copy itself is filled on the device.
 long long sliced_entries(const BinTable& bt);
 
-// Segment length for a matrix of nnz entries processed by `grid` blocks.
+// Segment length for a matrix of nnz entries processed by `grid` blocks (a
+// quarter of a block's mean share, at least 4096).
 int segment_length(long long nnz, int grid);
 
 // Cut the rows of the whole-block bin longer than seg_len into segments: they

@@ -1,6 +1,6 @@
 """The large power-law LP at full size (m = 2M, n = 5M, ~30M nonzeros), in
 the launch configuration the benchmark times (same grids, sliced and
-segmented bins, segments of ~33k entries), against the CPU oracle.
+segmented bins, segments of ~16k entries), against the CPU oracle.
 
 The oracle needs about a second per attempt at this size, so parity is
 checked on sampled outputs it can compute: the initial KKT check, then one
