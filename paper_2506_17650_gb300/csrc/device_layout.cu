@@ -4,6 +4,7 @@
 // the result equals the host's build_layout entry for entry.
 #include "device_layout.hpp"
 
+#include <algorithm>
 #include <climits>
 #include <type_traits>
 
