@@ -374,6 +374,34 @@ int alloc_vecs(lp_problem* p, Vecs<V>& v, int m, int n, bool values) {
   return LP_OK;
 }
 
+// Rows per sliced unit for a matrix whose units do not fill the grid: of
+// 256, 224, ..., 128 rows per thread column (units of twice that for the
+// two-rows-per-thread bins) the one (the largest on ties) that gives the
+// busiest SM the fewest rows -- its blocks times the rows of a unit -- with
+// every unit still resident at once.  The transport LP's 50,000 rows of A in
+// 206 units of 256 rows put two units on 54 SMs (512 rows); 192-row units put
+// at most 384 rows on an SM, and its 200,000 columns in units of 448 instead
+// of 512 at most 1,344 instead of 1,536 (a check-free attempt: 24.4 instead
+// of 26.0 us).  A matrix with
+// at least a grid's worth of units keeps 256 (fewer rows per unit would only
+// idle threads: 458 instead of 434 us per attempt on the power-law LP at 192).
+int sliced_unit_rows(const BinTable& bt, int cap, int sms) {
+  if (bt.nunits >= cap || sms < 1) return kBlock;
+  int best = kBlock;
+  long long best_load = -1;
+  for (int rows = kBlock; rows >= 128; rows -= 32) {
+    BinTable t = bt;
+    set_sliced_unit_rows(t, rows);
+    if (t.nunits > cap) continue;
+    const long long load = (long long)((t.nunits + sms - 1) / sms) * rows;
+    if (best_load < 0 || load < best_load) {
+      best_load = load;
+      best = rows;
+    }
+  }
+  return best;
+}
+
 // Device buffers and the layout: the CSR copies of A and A^T and the vectors
 // in bin order are built on the device from the caller's (valid, canonical)
 // arrays, with scratch taken from the arena and given back afterwards.
@@ -451,6 +479,8 @@ int upload(lp_problem* p, int m, int n, long long nz, const int64_t* row_ptr, co
   // grids from the unit counts; rows longer than half a block's share of the
   // work are then cut into segments, which adds units
   const int cap_d = sms * per_sm_d, cap_p = sms * per_sm_p;
+  set_sliced_unit_rows(d.binsA, sliced_unit_rows(d.binsA, cap_d, sms));
+  set_sliced_unit_rows(d.binsAt, sliced_unit_rows(d.binsAt, cap_p, sms));
   auto grid_of = [](int units, int cap) { return units < 1 ? 1 : (units < cap ? units : cap); };
   std::vector<int> segA = segment_long_rows(d.binsA, lay.A_head, segment_length(nz, grid_of(d.binsA.nunits, cap_d)));
   std::vector<int> segAt =

@@ -27,6 +27,7 @@
 
 #include "../../include/lpop.h"
 #include "common.cuh"
+#include "host_layout.hpp"
 #include "ops.cuh"
 #include "spmv.cuh"
 
@@ -407,6 +408,9 @@ int load_members(lp_batch* b, int count, lp_problem* const* members) {
     BCK(cudaSetDevice(v.device));
     BCK(cudaStreamSynchronize(v.stream));
     b->host_members[i].d = v.d;
+    // a team walks all of a member's units with its own threads: full units of kBlock rows
+    set_sliced_unit_rows(b->host_members[i].d.binsA, kBlock);
+    set_sliced_unit_rows(b->host_members[i].d.binsAt, kBlock);
     b->host_members[i].prm = v.prm;
     b->nnz[i] = v.d.nnz;
   }

@@ -129,6 +129,23 @@ BinTable make_bins(const std::vector<int>& widths_sorted, const std::vector<int>
   return bins_from_runs(runs);
 }
 
+void set_sliced_unit_rows(BinTable& bt, int rows) {
+  int unit = 0;
+  for (int b = 0; b < bt.nbins; ++b) {
+    Bin& x = bt.bin[b];
+    const int old_count = (b + 1 < bt.nbins ? bt.bin[b + 1].unit_begin : bt.nunits) - x.unit_begin;
+    if (x.width == kSell) x.unit_rows = rows == kBlock ? 0 : (x.len <= kPairMaxLen ? 2 * rows : rows);
+    x.unit_begin = unit;
+    if (x.width == kSegmented) {
+      unit += old_count;
+    } else {
+      const int per = rows_per_unit(x);
+      unit += (x.row_end - x.row_begin + per - 1) / per;
+    }
+  }
+  bt.nunits = unit;
+}
+
 long long sliced_entries(const BinTable& bt) {
   long long total = 0;
   for (int b = 0; b < bt.nbins; ++b) {
@@ -427,10 +444,10 @@ std::vector<int> segment_long_rows(BinTable& bt, const std::vector<int>& rp, int
   const int nseg_units = (int)units.size() / 2;
   BinTable out = bt;
   out.nbins = 0;
-  out.bin[out.nbins++] = Bin{blk.row_begin, r, kSegmented, 0, 0, 0};
+  out.bin[out.nbins++] = Bin{blk.row_begin, r, kSegmented, 0, 0, 0, 0};
   int unit = nseg_units;
   if (r < blk.row_end) {
-    out.bin[out.nbins++] = Bin{r, blk.row_end, 0, unit, 0, 0};
+    out.bin[out.nbins++] = Bin{r, blk.row_end, 0, unit, 0, 0, 0};
     unit += blk.row_end - r;
   }
   for (int b = 1; b < bt.nbins; ++b) {

@@ -65,6 +65,12 @@ BinTable bins_from_runs(const std::vector<BinRun>& runs);
 // >= target_threads / rows, capped at 8 (1 when the rows fill the GPU).
 int widen_factor(long long rows, long long target_threads);
 
+// Rows per thread column of a table's kSell bins: units of `rows` rows (a
+// multiple of 32 up to kBlock; kBlock is the default), 2 rows for the bins of
+// at most kPairMaxLen entries per row, with the units renumbered (a
+// segmented bin keeps its units).
+void set_sliced_unit_rows(BinTable& bt, int rows);
+
 // Entries of the sliced copy of a table's kSell bins (padding included); the
 // copy itself is filled on the device.
 long long sliced_entries(const BinTable& bt);

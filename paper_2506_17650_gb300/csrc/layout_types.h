@@ -33,7 +33,8 @@ enum Sched : int { kAdagrad = 0, kAdagradNorm = 1, kConst = 2 };
 // and an entry's position needs no row pointer.  Work units: one row per unit
 // for width 0, kBlock/width rows per unit for 1..32, one segment per unit for
 // kSegmented, kBlock rows per unit for kSell (2 kBlock, two rows per thread,
-// when len <= kPairMaxLen); units of all bins are numbered consecutively.
+// when len <= kPairMaxLen, or unit_rows rows when a matrix sets it); units of
+// all bins are numbered consecutively.
 constexpr int kSegmented = -1;
 constexpr int kSell = -2;
 
@@ -43,13 +44,14 @@ struct Bin {
   int width;
   int unit_begin;
   int len;         // kSell: entries per row
+  int unit_rows;   // kSell: rows per unit when set (0: the default below), a multiple of 32 (64 for pairs)
   long long base;  // kSell: position of the bin's first entry in the sliced copy
 };
 
 // Rows per work unit of a bin.
 LPOP_HD inline int rows_per_unit(const Bin& b) {
   if (b.width == 0 || b.width == kSegmented) return 1;
-  if (b.width == kSell) return b.len <= kPairMaxLen ? 2 * kBlock : kBlock;
+  if (b.width == kSell) return b.unit_rows > 0 ? b.unit_rows : (b.len <= kPairMaxLen ? 2 * kBlock : kBlock);
   return kBlock / b.width;
 }
 

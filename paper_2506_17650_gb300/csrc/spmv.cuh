@@ -143,11 +143,13 @@ __device__ __forceinline__ void sell_rows_at(const BinTable& bt, const Bin& B, i
   op.row(row, s);
 }
 
-// A unit of a kSell bin: thread t takes row local * kBlock + t of the bin.
+// A unit of a kSell bin: thread t < R takes row local * R + t of the bin (R
+// rows per unit: kBlock, or fewer when the matrix spreads its rows thinner).
 template <int NV, class V, class Acc, class Op>
 __device__ __forceinline__ void sell_rows(const BinTable& bt, const Bin& B, int local, const Gather<NV, V>& g,
                                           Op& op) {
-  sell_rows_at<NV, V, Acc>(bt, B, local * kBlock + (int)threadIdx.x, g, op);
+  const int R = rows_per_unit(B);
+  if ((int)threadIdx.x < R) sell_rows_at<NV, V, Acc>(bt, B, local * R + (int)threadIdx.x, g, op);
 }
 
 // A unit of a kSell bin of at most kPairMaxLen entries per row: thread t
@@ -160,8 +162,10 @@ template <int NV, class V, class Acc, class Op>
 __device__ __forceinline__ void sell_rows_pair(const BinTable& bt, const Bin& B, int local, const Gather<NV, V>& g,
                                                Op& op) {
   constexpr int C = kPairMaxLen;
-  const int i0 = local * (2 * kBlock) + (int)threadIdx.x;
-  const int i1 = i0 + kBlock;
+  const int H = rows_per_unit(B) / 2;  // rows per half unit: thread t < H takes rows t and H + t
+  if ((int)threadIdx.x >= H) return;
+  const int i0 = local * (2 * H) + (int)threadIdx.x;
+  const int i1 = i0 + H;
   const int r0 = B.row_begin + i0, r1 = B.row_begin + i1;
   if (r0 >= B.row_end) return;
   const bool v1 = r1 < B.row_end;
@@ -340,23 +344,26 @@ __device__ __forceinline__ void for_each_row_range(const BinTable& bt, const Csr
     switch (bt.bin[b].width) {
       case kSegmented: segment_unit<NV, V, Acc>(bt, local, M, g, op, smem, row_slots); break;
       case kSell:
-        if (bt.bin[b].len <= kPairMaxLen) {  // units of 2 kBlock rows
+        if (bt.bin[b].len <= kPairMaxLen) {  // units of two halves of H rows (H = kBlock by default)
+          const int H = rows_per_unit(bt.bin[b]) / 2;
           if (bt.sell_ci) {
             if constexpr (AllowsPair<Op>::value) {
               sell_rows_pair<NV, V, Acc>(bt, bt.bin[b], local, g, op);
-            } else {  // the unit's two halves one after the other
-              const int i0 = local * 2 * kBlock + (int)threadIdx.x;
+            } else if ((int)threadIdx.x < H) {  // the unit's two halves one after the other
+              const int i0 = local * 2 * H + (int)threadIdx.x;
               sell_rows_at<NV, V, Acc>(bt, bt.bin[b], i0, g, op);
-              sell_rows_at<NV, V, Acc>(bt, bt.bin[b], i0 + kBlock, g, op);
+              sell_rows_at<NV, V, Acc>(bt, bt.bin[b], i0 + H, g, op);
             }
           } else {
-            vec_rows<1, NV, V, Acc>(row_begin + local * 2 * kBlock, row_end, M, g, op);
-            vec_rows<1, NV, V, Acc>(row_begin + local * 2 * kBlock + kBlock, row_end, M, g, op);
+            const int h0 = row_begin + local * 2 * H;
+            vec_rows<1, NV, V, Acc>(h0, min(row_end, h0 + H), M, g, op);
+            vec_rows<1, NV, V, Acc>(h0 + H, min(row_end, h0 + 2 * H), M, g, op);
           }
         } else if (bt.sell_ci) {
           sell_rows<NV, V, Acc>(bt, bt.bin[b], local, g, op);
         } else {
-          vec_rows<1, NV, V, Acc>(row_begin + local * kBlock, row_end, M, g, op);
+          const int R = rows_per_unit(bt.bin[b]);
+          vec_rows<1, NV, V, Acc>(row_begin + local * R, min(row_end, row_begin + (local + 1) * R), M, g, op);
         }
         break;
       case 0: block_row<NV, V, Acc>(row_begin + local, M, g, op, smem); break;
