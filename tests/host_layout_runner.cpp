@@ -1,9 +1,10 @@
 // Test program for the library's host-side layout code (csrc/host_layout.cpp):
 // reads a CSR matrix from three raw files, runs build_layout (and optionally
-// segment_long_rows on both bin tables), and writes everything it produced to
-// one raw file that tests/test_host_layout.py reads back and checks.
+// segment_long_rows on both bin tables, then set_sliced_unit_rows), and writes
+// everything it produced to one raw file that tests/test_host_layout.py reads
+// back and checks.
 //
-//   host_layout_runner m n nnz in_prefix out_path target_threads seg_len
+//   host_layout_runner m n nnz in_prefix out_path target_threads seg_len [sliced_rows]
 //
 // Input files: <in_prefix>rp.bin (int64 [m+1]), ci.bin (int32 [nnz]),
 // v.bin (float64 [nnz]).  seg_len <= 0 skips the segmentation.
@@ -63,10 +64,11 @@ void put_bins(FILE* f, const lpop::BinTable& bt) {
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc != 8) {
-    std::fprintf(stderr, "usage: %s m n nnz in_prefix out_path target_threads seg_len\n", argv[0]);
+  if (argc != 8 && argc != 9) {
+    std::fprintf(stderr, "usage: %s m n nnz in_prefix out_path target_threads seg_len [sliced_rows]\n", argv[0]);
     return 2;
   }
+  const int sliced_rows = argc == 9 ? std::atoi(argv[8]) : 0;
   const int m = std::atoi(argv[1]), n = std::atoi(argv[2]);
   const long long nnz = std::atoll(argv[3]);
   const std::string pre = argv[4];
@@ -84,6 +86,10 @@ int main(int argc, char** argv) {
   if (rc == 0 && seg_len > 0) {
     segA = lpop::segment_long_rows(lay.binsA, lay.A_rp, seg_len);
     segAt = lpop::segment_long_rows(lay.binsAt, lay.At_rp, seg_len);
+  }
+  if (rc == 0 && sliced_rows > 0) {
+    lpop::set_sliced_unit_rows(lay.binsA, sliced_rows);
+    lpop::set_sliced_unit_rows(lay.binsAt, sliced_rows);
   }
   FILE* o = std::fopen(argv[5], "wb");
   if (!o) return 2;

@@ -11,7 +11,8 @@ against scipy.sparse and against the layout's own definition:
 * the bins cover the rows contiguously, longest rows first, with the unit
   numbering and the sliced-copy offsets their rows imply;
 * invalid input is rejected with the first offending index;
-* segmentation cuts exactly the rows longer than the segment length.
+* segmentation cuts exactly the rows longer than the segment length;
+* smaller sliced units renumber the units and change nothing else.
 """
 import os
 import shutil
@@ -64,13 +65,14 @@ class _Reader:
                     bins=[dict(zip(("row_begin", "row_end", "width", "unit_begin", "len", "base"), r)) for r in rows])
 
 
-def run_layout(runner, tmp_path, m, n, rp, ci, v, target=0, seg_len=0):
+def run_layout(runner, tmp_path, m, n, rp, ci, v, target=0, seg_len=0, sliced_rows=0):
     pre = str(tmp_path / "in_")
     np.asarray(rp, np.int64).tofile(pre + "rp.bin")
     np.asarray(ci, np.int32).tofile(pre + "ci.bin")
     np.asarray(v, np.float64).tofile(pre + "v.bin")
     out = str(tmp_path / "out.bin")
-    subprocess.run([runner, str(m), str(n), str(len(ci)), pre, out, str(target), str(seg_len)], check=True)
+    extra = [str(sliced_rows)] if sliced_rows else []
+    subprocess.run([runner, str(m), str(n), str(len(ci)), pre, out, str(target), str(seg_len), *extra], check=True)
     r = _Reader(open(out, "rb").read())
     rc = r.take("<i")
     n_err = r.take("<i")
@@ -84,17 +86,17 @@ def run_layout(runner, tmp_path, m, n, rp, ci, v, target=0, seg_len=0):
     return lay
 
 
-def rows_per_unit(width, length=None):
+def rows_per_unit(width, length=None, sliced_rows=K_BLOCK):
     if width in (0, K_SEGMENTED):
         return 1
     if width == K_SELL and length is not None and length <= K_PAIR_MAX:
-        return 2 * K_BLOCK
+        return 2 * sliced_rows
     if width == K_SELL:
-        return K_BLOCK
+        return sliced_rows
     return K_BLOCK // width
 
 
-def check_bins(bt, rp, rows):
+def check_bins(bt, rp, rows, sliced_rows=K_BLOCK):
     lens = np.diff(rp)
     assert np.all(np.diff(lens) <= 0), "rows are not in non-increasing length order"
     at, unit, sliced = 0, 0, 0
@@ -107,7 +109,7 @@ def check_bins(bt, rp, rows):
             nseg = int(np.sum((seg + bt["seg_len"] - 1) // bt["seg_len"]))
             unit += nseg
         else:
-            unit += -(-(b["row_end"] - b["row_begin"]) // rows_per_unit(w, b["len"]))
+            unit += -(-(b["row_end"] - b["row_begin"]) // rows_per_unit(w, b["len"], sliced_rows))
         if w == K_SELL:
             assert np.all(seg == b["len"]) and 0 <= b["len"] <= K_SELL_MAX  # empty rows form a bin of length 0
             assert b["base"] == sliced
@@ -246,3 +248,29 @@ def test_empty_rows_and_no_constraints(runner, tmp_path):
     assert lay["rc"] == 0 and lay["nnz"] == 0 and sorted(lay["pcol"]) == list(range(5))
     lay = run_layout(runner, tmp_path, 4, 3, [0, 0, 2, 2, 3], [2, 0, 1], [1.0, 2.0, 3.0])
     check_layout(lay, 4, 3, sp.csr_matrix(([1.0, 2.0, 3.0], [2, 0, 1], [0, 0, 2, 2, 3]), shape=(4, 3)))
+
+
+@pytest.mark.parametrize("case", ["long_rows", "transport"])
+@pytest.mark.parametrize("rows", [224, 192, 128])
+def test_smaller_sliced_units_renumber_only_the_units(runner, tmp_path, case, rows):
+    """set_sliced_unit_rows: units of `rows` rows (of twice that for the bins
+    of at most two entries per row, two rows per thread), a segmented bin
+    keeping its units; every other field of the tables is unchanged, and
+    back at 256 rows the tables are the default ones again."""
+    lp = CASES[case]()
+    args = (lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val)
+    base = run_layout(runner, tmp_path, *args, seg_len=4096)
+    lay = run_layout(runner, tmp_path, *args, seg_len=4096, sliced_rows=rows)
+    back = run_layout(runner, tmp_path, *args, seg_len=4096, sliced_rows=K_BLOCK)
+    sliced = 0
+    for bt_key, rp_key in (("binsA", "A_rp"), ("binsAt", "At_rp")):
+        check_bins(lay[bt_key], lay[rp_key], len(lay[rp_key]) - 1, sliced_rows=rows)
+        assert back[bt_key] == base[bt_key]
+        for b0, b1 in zip(base[bt_key]["bins"], lay[bt_key]["bins"]):
+            assert {k: v for k, v in b0.items() if k != "unit_begin"} == {k: v for k, v in b1.items() if k != "unit_begin"}
+            sliced += b0["width"] == K_SELL
+        assert lay[bt_key]["nunits"] >= base[bt_key]["nunits"]
+        assert lay[bt_key]["sliced"] == base[bt_key]["sliced"]
+    assert sliced > 0
+    for key in ("segA", "segAt"):
+        assert np.array_equal(lay[key], base[key])
