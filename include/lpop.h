@@ -124,7 +124,9 @@ typedef struct lp_options {
   int32_t refine_stall;            /* mixed: the FP32 phase also hands over after this many checks in a
                                       row without a 10% drop of its best relative KKT error; >= 1,
                                       default 16 */
-  int32_t reserved;                /* must be zero */
+  int32_t log_every;               /* > 0: lp_solve writes one line to stderr every log_every KKT checks
+                                      (attempts, accepted steps, restarts, the three relative KKT errors,
+                                      objectives, eta, omega, precision phase); 0 (default): silent */
 } lp_options;
 
 typedef struct lp_stats {

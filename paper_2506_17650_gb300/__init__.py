@@ -66,7 +66,7 @@ class LpOptions(ctypes.Structure):
         ("device_free", c_void_p),
         ("alloc_ctx", c_void_p),
         ("refine_stall", c_int32),
-        ("reserved", c_int32),
+        ("log_every", c_int32),
     ]
 
 

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -78,6 +79,7 @@ struct lp_problem {
   // are final
   long long sell_n[2] = {0, 0};
   RuizSplit ruiz[2] = {};  // how the Ruiz kernels cut the rows of A / A^T
+  long long checks_seen = 0;  // KKT checks run by lp_solve since create (for log_every)
   int* sell_ci[2] = {nullptr, nullptr};
   double* sell_v[2] = {nullptr, nullptr};
   float* sell_v32[2] = {nullptr, nullptr};
@@ -197,7 +199,7 @@ int check_options(const lp_options& o, std::string& msg) {
   if (o.refine_stall < 1) return msg = "refine_stall must be >= 1", 1;
   if ((o.device_alloc == nullptr) != (o.device_free == nullptr))
     return msg = "device_alloc and device_free must be given together", 1;
-  if (o.reserved != 0) return msg = "the reserved option field must be zero", 1;
+  if (o.log_every < 0) return msg = "log_every must be >= 0", 1;
   return 0;
 }
 
@@ -255,6 +257,7 @@ double read_scalar(lp_problem* p, const double* dptr, int* rc) {
 }
 
 int preprocess(lp_problem* p) {
+  NvtxRange range("lpop preprocess");
   Dev& d = p->d;
   cudaStream_t s = p->stream;
   const int m = d.m, n = d.n;
@@ -439,6 +442,7 @@ int upload(lp_problem* p, int m, int n, long long nz, const int64_t* row_ptr, co
     const LayoutArrays arr{d.A_rp, d.A_ci, d.A_v, d.At_rp, d.At_ci, d.At_v, p->d_prow, p->d_pcol};
     const LayoutVectors vecs{b, c, lb, ub, sense, d.f64.b, d.f64.c, d.f64.l, d.f64.u, d.sense};
     std::string msg;
+    NvtxRange range("lpop layout");
     // FP64 rows take one lane up to kSellMaxLen entries whatever the matrix size (widen 1):
     // extra lanes cost FP64 shuffle adds, which outweigh the added parallelism on GB300
     const int rc = build_layout_device(m, n, nz, row_ptr, col_idx, val, 1, 1, arr, &vecs, lay, scratch, p->stream, msg);
@@ -894,6 +898,20 @@ int certify_fp32(lp_problem* p, int* status) {
   return read_status(p, status);
 }
 
+// One line on stderr per log_every checks: the state the last check left.
+int maybe_log(lp_problem* p) {
+  if (p->opt.log_every <= 0 || ++p->checks_seen % p->opt.log_every != 0) return LP_OK;
+  DevState hs;
+  CK(cudaMemcpyAsync(&hs, p->d.st, sizeof(hs), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  std::fprintf(stderr,
+               "lpop: attempts %lld accepted %lld restarts %lld rel_pres %.3e rel_dres %.3e rel_gap %.3e "
+               "pobj %.10g dobj %.10g eta %.4e omega %.4e %s\n",
+               hs.attempts, hs.k, hs.restarts, hs.rel_pres, hs.rel_dres, hs.rel_gap, hs.pobj, hs.dobj, hs.eta,
+               hs.omega, p->fp32_phase ? "fp32" : "fp64");
+  return LP_OK;
+}
+
 int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_out) {
   TRY(select_device(p));
   const auto t0 = std::chrono::steady_clock::now();
@@ -911,9 +929,11 @@ int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_ou
     p->initial_check_done = true;
     TRY(read_status(p, &status));
     TRY(certify_fp32(p, &status));
+    TRY(maybe_log(p));
   }
   int out_status = LP_STATUS_NONE;
   while (status == 0 && p->host_attempts < iter_limit) {
+    NvtxRange period("lpop check period");
     const bool fp32 = p->fp32_phase;
     const long long to_boundary = ce - p->host_attempts % ce;
     const long long remaining = iter_limit - p->host_attempts;
@@ -944,6 +964,7 @@ int solve_impl(lp_problem* p, double tol, int64_t iter_limit, int32_t* status_ou
       TRY(read_status(p, &status));
     }
     TRY(certify_fp32(p, &status));
+    if (checked) TRY(maybe_log(p));
     if (status == 0 && checked) TRY(maybe_refine(p));
     if (p->opt.time_limit > 0.0) {
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1030,6 +1051,7 @@ void lp_options_default(lp_options* o) {
   o->precision = LP_PREC_FP64;
   o->refine_tol = 1e-6;
   o->refine_stall = 16;
+  o->log_every = 0;
 }
 
 const char* lp_last_error(const lp_problem* p) {
@@ -1041,6 +1063,7 @@ int lp_create(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const i
               const double* b, const double* c, const double* lb, const double* ub, const char* sense,
               const lp_options* opt, lp_problem** out) {
   try {
+    NvtxRange range("lpop create");
     return create_impl(m, n, nnz, row_ptr, col_idx, val, b, c, lb, ub, sense, opt, out);
   } catch (const std::exception& ex) {
     return set_err(nullptr, LP_ERR_OOM, std::string("host exception: ") + ex.what());
@@ -1052,6 +1075,7 @@ int lp_solve(lp_problem* p, double rel_kkt_tol, int64_t iter_limit, int32_t* sta
   if (!(rel_kkt_tol >= 0.0)) return set_err(p, LP_ERR_INVALID_ARG, "rel_kkt_tol must be >= 0");
   if (iter_limit < 0) return set_err(p, LP_ERR_INVALID_ARG, "iter_limit must be >= 0");
   try {
+    NvtxRange range("lpop solve");
     return solve_impl(p, rel_kkt_tol, iter_limit, status_out);
   } catch (const std::exception& ex) {
     return set_err(p, LP_ERR_OOM, std::string("host exception: ") + ex.what());

@@ -630,6 +630,7 @@ int lp_batch_set_schedule(lp_batch* b, int32_t cluster_size, int64_t wide_nnz) {
 int lp_batch_round(lp_batch* b, double rel_kkt_tol, int32_t attempts, int64_t iter_limit, int32_t* active_out) {
   if (!b) return berr(nullptr, LP_ERR_INVALID_ARG, "batch handle is NULL");
   if (attempts < 1 || !(rel_kkt_tol >= 0.0)) return berr(b, LP_ERR_INVALID_ARG, "need attempts >= 1 and tol >= 0");
+  NvtxRange range("lpop batch round");
   BCK(cudaSetDevice(b->device));
   const int count = (int)b->probs.size();
   if (count == 0) {

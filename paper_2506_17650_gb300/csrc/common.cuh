@@ -11,9 +11,20 @@
 
 #include <cmath>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "layout_types.h"
 
 namespace lpop {
+
+// A named NVTX range for the lifetime of the object (the library's phases
+// show up in profilers; costs nothing measurable when no tool listens).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 template <class V>
 struct CsrT {

@@ -520,3 +520,27 @@ def test_invalid_input_rejected_before_device_work():
     with pytest.raises(lpop.LpError) as ei:
         lpop.lp_create(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, b, lp.c, lp.lb, lp.ub, lp.sense)
     assert ei.value.code == lpop.LP_ERR_INVALID_INPUT
+
+
+def test_log_every_writes_one_line_per_check(capfd):
+    """log_every = k: lp_solve writes a line after every k-th KKT check (the
+    initial check counts), holding that check's figures."""
+    lp = lpgen.tiny_random(0)
+    for every in (1, 3):
+        with lpop.Problem(lp, alpha=1e-3, phi=20, log_every=every) as p:
+            assert p.solve(1e-4, 100_000) == lpop.LP_OPTIMAL
+            _, _, s = p.result(want_x=False, want_y=False)
+        lines = [l.split() for l in capfd.readouterr().err.splitlines() if l.startswith("lpop: ")]
+        checks = 1 + s["iterations"] // 64
+        assert len(lines) == checks // every
+        for k, l in enumerate(lines):
+            assert int(l[l.index("attempts") + 1]) == 64 * (every * (k + 1) - 1)
+            assert l[-1] == "fp64"
+        if every == 1:
+            last = lines[-1]
+            assert int(last[last.index("accepted") + 1]) == s["accepted"]
+            for key in ("rel_pres", "rel_dres", "rel_gap"):
+                assert float(last[last.index(key) + 1]) == pytest.approx(s[key], rel=1e-3, abs=1e-300)
+    with lpop.Problem(lp, alpha=1e-3, phi=20) as p:  # silent by default
+        p.solve(1e-4, 100_000)
+    assert "lpop: " not in capfd.readouterr().err

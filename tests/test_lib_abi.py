@@ -51,6 +51,7 @@ def test_options_default(lib):
     assert o.phi == 20 and o.normalize == 1 and o.check_every == 64
     assert o.ruiz_iters == 10 and o.pc_beta == 1.0 and o.precond_floor == 1e-6
     assert o.alpha == 0.0 and o.use_graph == 1 and o.restart == 1
+    assert o.refine_stall == 16 and o.log_every == 0
     assert ctypes.sizeof(lpop.LpOptions) == ctypes.sizeof(o)
 
 
@@ -101,7 +102,8 @@ def test_invalid_input_is_rejected_on_the_host(lib, what):
 @pytest.mark.parametrize("field,value", [("mode", 7), ("scheduler", 5), ("alpha", -1.0), ("check_every", 0),
                                          ("check_every", (1 << 16) + 1),
                                          ("precond_floor", 0.0), ("pc_beta", 3.0), ("ruiz_iters", -1),
-                                         ("kernel_timing", -1), ("device_alloc", 4096), ("device_free", 4096)])
+                                         ("kernel_timing", -1), ("device_alloc", 4096), ("device_free", 4096),
+                                         ("refine_stall", 0), ("log_every", -1)])
 def test_invalid_options_are_rejected(lib, field, value):
     lp = lpgen.mixed_small(0, m=12, n=20)
     opts = lpop.lp_options_default()
