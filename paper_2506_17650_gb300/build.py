@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblpop.so")
+LIB_CHECKED = os.path.join(HERE, "liblpop_checked.so")
 
 SOURCES = ["api.cu", "kernels_iter.cu", "kernels_check.cu", "kernels_setup.cu", "host_layout.cpp", "device_layout.cu",
            "noalloc.cu", "batch.cu"]
@@ -30,9 +31,9 @@ def nvcc() -> str:
     return path
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-pthread",
+def _compile(src: str, verbose_ptxas: bool, build_dir: str = BUILD, defines=()) -> str:
+    obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-pthread", *defines,
            "-I", os.path.join(HERE, "..", "include"), "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["--expt-relaxed-constexpr"]
@@ -46,23 +47,29 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
-def build(verbose_ptxas: bool = False, force: bool = False) -> str:
-    """Compile and link; returns the path of the shared library."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose_ptxas: bool = False, force: bool = False, checked: bool = False) -> str:
+    """Compile and link; returns the path of the shared library.  checked=True
+    builds the debug variant liblpop_checked.so instead (-DLPOP_CHECK_BOUNDS:
+    every gather's index checked against the vector it reads, violations
+    counted and skipped; read with lpop_bad_gathers)."""
+    lib_path = LIB_CHECKED if checked else LIB
+    build_dir = BUILD + "_checked" if checked else BUILD
+    os.makedirs(build_dir, exist_ok=True)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "lpop.h")]
-    if not force and os.path.exists(LIB):
-        lib_mtime = os.path.getmtime(LIB)
+    if not force and os.path.exists(lib_path):
+        lib_mtime = os.path.getmtime(lib_path)
         if all(os.path.getmtime(d) <= lib_mtime for d in deps):
-            return LIB
+            return lib_path
+    defines = ("-DLPOP_CHECK_BOUNDS",) if checked else ()
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas, build_dir, defines), SOURCES))
+    tmp = lib_path + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"linking failed:\n{' '.join(cmd)}\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -467,6 +467,8 @@ int upload(lp_problem* p, int m, int n, long long nz, const int64_t* row_ptr, co
   TRY(dalloc(p, &d.work2, (size_t)(m > n ? m : n) + 1));
   TRY(dalloc(p, &d.work, (size_t)m + n + 2048));
   TRY(dalloc(p, &d.st, 1));
+  TRY(dalloc(p, &d.bad_gathers, 1));
+  CK(cudaMemsetAsync(d.bad_gathers, 0, sizeof(unsigned int), p->stream));
   {
     cudaError_t te = cudaSuccess;
     d.step_tab = step_table(p->device, p->stream, &te);
@@ -1192,6 +1194,7 @@ int lp_memory_bytes(int32_t m, int32_t n, int64_t nnz, const lp_options* opt, in
   t += 13 * r(8LL * m) + 12 * r(8LL * n);                                          // FP64 vector set
   if (o.precision == LP_PREC_MIXED) t += 2 * r(4LL * nnz) + 13 * r(4LL * m) + 12 * r(4LL * n);  // FP32 set
   t += r(8LL * (m > n ? m : n) + 8) + r(m) + r(8LL * ((long long)m + n + 2048)) + r(sizeof(DevState));
+  t += r(4);  // count of out-of-range gathers (checked builds)
   // segmented rows (segments are at least 4096 entries): at most S rows and 2 S units per matrix
   const long long S = nnz / 4096 + 1;
   t += 2 * (r(8LL * 2 * S) + r(16LL * 2 * S) + r(4LL * S));
@@ -1218,6 +1221,19 @@ int lp_kernel_times(lp_problem* p, double* ms, int64_t* samples, int32_t n_kerne
 }
 
 void lp_destroy(lp_problem* p) { release(p); }
+
+#ifdef LPOP_CHECK_BOUNDS
+// Checked builds only (not declared in lpop.h): gathers of the problem's
+// kernels whose column index fell outside the gathered vector, counted and
+// skipped instead of read.
+int lpop_bad_gathers(lp_problem* p, unsigned long long* count) {
+  if (!p || !count) return LP_ERR_INVALID_ARG;
+  unsigned int h = 0;
+  if (cudaMemcpy(&h, p->d.bad_gathers, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return LP_ERR_CUDA;
+  *count = h;
+  return LP_OK;
+}
+#endif
 
 }  // extern "C"
 

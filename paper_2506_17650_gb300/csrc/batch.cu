@@ -114,6 +114,8 @@ __device__ void team_check(const Dev& d, const Params& prm, DevState& s, int ran
     Gather<2, V> g;
     g.x[0] = v.y[cur];
     g.x[1] = v.ybar[cur];
+    g.n = d.m;
+    g.bad = d.bad_gathers;
     for_each_row_range<2, V, double>(d.binsAt, csr_at<V>(d), g, op, blk, rank, T);
 #pragma unroll
     for (int q = 0; q < 10; ++q) p1[q] = op.acc[q];
@@ -127,6 +129,8 @@ __device__ void team_check(const Dev& d, const Params& prm, DevState& s, int ran
     for (int q = 0; q < 10; ++q) op.acc[q] = 0.0;
     Gather<1, V> g;
     g.x[0] = v.y[cur];
+    g.n = d.m;
+    g.bad = d.bad_gathers;
     for_each_row_range<1, V, double>(d.binsAt, csr_at<V>(d), g, op, blk, rank, T);
 #pragma unroll
     for (int q = 0; q < 10; ++q) p1[q] = op.acc[q];
@@ -144,6 +148,8 @@ __device__ void team_check(const Dev& d, const Params& prm, DevState& s, int ran
     if (prm.mode == kPdlp) {
       Gather<1, V> g;
       g.x[0] = v.xbar[cur];
+      g.n = d.n;
+      g.bad = d.bad_gathers;
       for_each_row_range<1, V, double>(d.binsA, csr_a<V>(d), g, op, blk, rank, T);
     } else {
       const double s0[1] = {0.0};
@@ -191,6 +197,8 @@ __device__ void team_promote(const Dev& d, const DevState& s, int rank, int T, b
   StoreRowOp op{b.ax[cur]};
   Gather<1, double> g;
   g.x[0] = b.x[cur];
+  g.n = d.n;
+  g.bad = d.bad_gathers;
   for_each_row_range<1, double, double>(d.binsA, d.A, g, op, blk, rank, T);
   team_sync(wide);
 }
@@ -238,6 +246,8 @@ __device__ bool team_round(const Member& mb, DevState& s, int& budget, int rank,
       op.acc[0] = op.acc[1] = op.acc[2] = V(0);
       Gather<1, V> g;
       g.x[0] = v.y[cur];
+      g.n = d.m;
+      g.bad = d.bad_gathers;
       for_each_row_range<1, V, V>(d.binsAt, csr_at<V>(d), g, op, blk, rank, T);
       t1[0] = op.acc[0]; t1[1] = op.acc[1]; t1[2] = op.acc[2];
     }
@@ -254,6 +264,8 @@ __device__ bool team_round(const Member& mb, DevState& s, int& budget, int rank,
       op.acc[0] = op.acc[1] = op.acc[2] = op.acc[3] = V(0);
       Gather<1, V> g;
       g.x[0] = v.x[nxt];
+      g.n = d.n;
+      g.bad = d.bad_gathers;
       for_each_row_range<1, V, V>(d.binsA, csr_a<V>(d), g, op, blk, rank, T);
       t2[0] = op.acc[0]; t2[1] = op.acc[1]; t2[2] = op.acc[2]; t2[3] = op.acc[3];
     }

@@ -174,6 +174,7 @@ struct Dev {
   double* work2;      // [max(m, n)] FP64 staging of FP32 vectors read by the host
   const double* step_tab;  // [2 * kStepTab]: 1 - (t+1)^-0.3 and 1 + (t+1)^-0.6 for t < kStepTab
   DevState* st;
+  unsigned int* bad_gathers;  // checked builds: gathers whose index fell outside the vector
   BinTable binsA, binsAt;
   int gridA, gridAt;      // blocks launched for the A / A^T row kernels (FP64)
   int gridA32, gridAt32;  // the same for the FP32 kernels (fewer registers, more resident blocks)

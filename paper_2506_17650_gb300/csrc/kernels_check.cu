@@ -46,6 +46,8 @@ __global__ void __launch_bounds__(kBlock, kCheckBlocksPerSm<V>) check_primal_ker
   Gather<NV, V> g;
   g.x[0] = v.y[cur];
   if (NV > 1) g.x[NV - 1] = v.ybar[cur];
+  g.n = d.m;
+  g.bad = d.bad_gathers;
   for_each_row<NV, V, double>(d.binsAt, csr_at<V>(d), g, op, smem, row_slots_at<V>(d, d.partials));
   block_sum_smem<10>(op.acc, smem);
   if (threadIdx.x == 0) {
@@ -78,6 +80,8 @@ __global__ void __launch_bounds__(kBlock, kCheckBlocksPerSm<V>) check_dual_kerne
   if (AVG) {
     Gather<1, V> g;
     g.x[0] = v.xbar[cur];
+    g.n = d.n;
+    g.bad = d.bad_gathers;
     for_each_row<1, V, double>(d.binsA, csr_a<V>(d), g, op, smem, row_slots_a<V>(d, d.partials2));
   } else {
     // without an average candidate only the cached A x is needed: no sparse product

@@ -52,6 +52,8 @@ __global__ void __launch_bounds__(kBlock, kStepBlocksPerSm<V>) primal_step_kerne
   op.acc[0] = op.acc[1] = op.acc[2] = V(0);
   Gather<1, V> g;
   g.x[0] = v.y[cur];
+  g.n = d.m;
+  g.bad = d.bad_gathers;
   for_each_row<1, V, V>(d.binsAt, csr_at<V>(d), g, op, smem, row_slots_at<V>(d, d.partials));
   double a[3] = {(double)op.acc[0], (double)op.acc[1], (double)op.acc[2]};
   block_sum_smem<3>(a, smem);
@@ -90,6 +92,8 @@ __global__ void __launch_bounds__(kBlock, kStepBlocksPerSm<V>) dual_step_kernel(
   op.acc[0] = op.acc[1] = op.acc[2] = op.acc[3] = V(0);
   Gather<1, V> g;
   g.x[0] = v.x[nxt];  // x+ written by the primal kernel
+  g.n = d.n;
+  g.bad = d.bad_gathers;
   for_each_row<1, V, V>(d.binsA, csr_a<V>(d), g, op, smem, row_slots_a<V>(d, d.partials2));
   double a[4] = {(double)op.acc[0], (double)op.acc[1], (double)op.acc[2], (double)op.acc[3]};
   block_sum_smem<4>(a, smem);

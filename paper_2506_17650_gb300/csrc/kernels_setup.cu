@@ -360,6 +360,8 @@ __global__ void __launch_bounds__(kBlock) recompute_ax_kernel(Dev d) {
   StoreCurOp op{d.f64.ax[cur]};
   Gather<1, double> g;
   g.x[0] = d.f64.x[cur];
+  g.n = d.n;
+  g.bad = d.bad_gathers;
   for_each_row<1, double, double>(d.binsA, d.A, g, op, smem);
 }
 

@@ -22,7 +22,22 @@ namespace lpop {
 template <int NV, class V>
 struct Gather {
   const V* x[NV];
+  int n = 0x7fffffff;            // entries of each x (checked builds reject indices beyond)
+  unsigned int* bad = nullptr;   // checked builds: count of rejected indices
 };
+
+// x[q][c].  Built with LPOP_CHECK_BOUNDS (the debug build the tests use), an
+// index outside [0, n) is counted in *bad and reads 0 instead of memory.
+template <int NV, class V>
+__device__ __forceinline__ V gather(const Gather<NV, V>& g, int q, int c) {
+#ifdef LPOP_CHECK_BOUNDS
+  if ((unsigned)c >= (unsigned)g.n) {
+    if (g.bad) atomicAdd(g.bad, 1u);
+    return V(0);
+  }
+#endif
+  return __ldg(g.x[q] + c);
+}
 
 // Ops that keep per-block reduction accumulators (member `acc`).
 template <class Op, class = void>
@@ -63,7 +78,7 @@ __device__ __forceinline__ void chunk_dot(int k0, int end, int stride, const Csr
   for (int q = 0; q < NV; ++q) {
     Acc xv[kChunk];
 #pragma unroll
-    for (int u = 0; u < kChunk; ++u) xv[u] = c[u] >= 0 ? (Acc)__ldg(g.x[q] + c[u]) : Acc(0);
+    for (int u = 0; u < kChunk; ++u) xv[u] = c[u] >= 0 ? (Acc)gather(g, q, c[u]) : Acc(0);
 #pragma unroll
     for (int u = 0; u < kChunk; ++u) {
       if (u >= most) break;
@@ -132,7 +147,7 @@ __device__ __forceinline__ void sell_rows_at(const BinTable& bt, const Bin& B, i
     for (int q = 0; q < NV; ++q) {
       Acc xv[kChunk];
 #pragma unroll
-      for (int u = 0; u < kChunk; ++u) xv[u] = u < nk ? (Acc)__ldg(g.x[q] + c[u]) : Acc(0);
+      for (int u = 0; u < kChunk; ++u) xv[u] = u < nk ? (Acc)gather(g, q, c[u]) : Acc(0);
 #pragma unroll
       for (int u = 0; u < kChunk; ++u) {
         if (u >= nk) break;
@@ -198,8 +213,8 @@ __device__ __forceinline__ void sell_rows_pair(const BinTable& bt, const Bin& B,
     Acc x0[C], x1[C];
 #pragma unroll
     for (int u = 0; u < C; ++u) {
-      x0[u] = u < L ? (Acc)__ldg(g.x[q] + c0[u]) : Acc(0);
-      x1[u] = u < L && v1 ? (Acc)__ldg(g.x[q] + c1[u]) : Acc(0);
+      x0[u] = u < L ? (Acc)gather(g, q, c0[u]) : Acc(0);
+      x1[u] = u < L && v1 ? (Acc)gather(g, q, c1[u]) : Acc(0);
     }
     s0[q] = Acc(0);
     s1[q] = Acc(0);
