@@ -2,6 +2,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -187,34 +188,46 @@ int validate_csr(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, cons
     err = "row_ptr[0] must be 0 and row_ptr[m] must equal nnz";
     return LP_ERR_INVALID_INPUT;
   }
-  for (int i = 0; i < m; ++i) {
-    if (row_ptr[i + 1] < row_ptr[i]) {
-      err = "row_ptr must be non-decreasing (row " + std::to_string(i) + ")";
-      return LP_ERR_INVALID_INPUT;
-    }
+  const long long dec = first_bad_index(m, [&](long long i) { return row_ptr[i + 1] < row_ptr[i]; });
+  if (dec < m) {
+    err = "row_ptr must be non-decreasing (row " + std::to_string(dec) + ")";
+    return LP_ERR_INVALID_INPUT;
   }
   // entries (on host threads, by ranges of rows): the first one with a column
   // out of range or a value that is not finite, and whether every row is in
-  // strictly increasing column order
+  // strictly increasing column order.  A range is first passed without
+  // branches (columns and exponent bits tested, column descents counted, the
+  // descents across row starts taken off again); only a range with a bad
+  // entry is walked again for its first one.
   canonical = true;
   {
     std::mutex mu;
     int64_t bad = nnz;
     auto scan = [&](long long r0, long long r1) {
+      const int64_t k0 = row_ptr[r0], k1 = row_ptr[r1];
+      unsigned any_bad = 0;
+      long long desc = 0;
+      for (int64_t k = k0; k < k1; ++k) {
+        uint64_t bits;
+        std::memcpy(&bits, val + k, sizeof(bits));
+        any_bad |= (unsigned)((uint32_t)col_idx[k] >= (uint32_t)n) |
+                   (unsigned)((bits & 0x7ff0000000000000ULL) == 0x7ff0000000000000ULL);
+      }
+      for (int64_t k = k0 + 1; k < k1; ++k) desc += col_idx[k - 1] >= col_idx[k];
+      for (long long i = r0 + 1; i < r1; ++i) {  // each distinct row start inside the range once
+        const int64_t st = row_ptr[i];
+        if (st > k0 && st < k1 && st != row_ptr[i - 1]) desc -= col_idx[st - 1] >= col_idx[st];
+      }
       int64_t first_bad = nnz;
-      bool inc = true;
-      for (long long i = r0; i < r1 && first_bad == nnz; ++i) {
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-          if (col_idx[k] < 0 || col_idx[k] >= n || !std::isfinite(val[k])) {
-            first_bad = k;
-            break;
-          }
-          inc = inc && (k == row_ptr[i] || col_idx[k - 1] < col_idx[k]);
+      for (int64_t k = k0; any_bad && k < k1; ++k) {
+        if (col_idx[k] < 0 || col_idx[k] >= n || !std::isfinite(val[k])) {
+          first_bad = k;
+          break;
         }
       }
       std::lock_guard<std::mutex> lock(mu);
       bad = std::min(bad, first_bad);
-      canonical = canonical && inc;
+      canonical = canonical && desc == 0;
     };
     parallel_ranges(m, scan, nnz);
     if (bad < nnz) {
