@@ -7,7 +7,9 @@
 //   host_layout_runner m n nnz in_prefix out_path target_threads seg_len [sliced_rows]
 //
 // Input files: <in_prefix>rp.bin (int64 [m+1]), ci.bin (int32 [nnz]),
-// v.bin (float64 [nnz]).  seg_len <= 0 skips the segmentation.
+// v.bin (float64 [nnz]).  seg_len <= 0 skips the segmentation.  sliced_rows
+// = -1 runs validate_csr alone and writes rc, the message and the canonical
+// flag (int32 each, the message as its length and bytes).
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -77,6 +79,20 @@ int main(int argc, char** argv) {
   const auto rp = read_all<long long>(pre + "rp.bin", (size_t)m + 1);
   const auto ci = read_all<int>(pre + "ci.bin", (size_t)nnz);
   const auto v = read_all<double>(pre + "v.bin", (size_t)nnz);
+  if (sliced_rows == -1) {
+    bool canonical = false;
+    std::string err;
+    const int rc = lpop::validate_csr(m, n, nnz, reinterpret_cast<const int64_t*>(rp.data()), ci.data(), v.data(),
+                                      canonical, err);
+    FILE* o = std::fopen(argv[5], "wb");
+    if (!o) return 2;
+    put<int>(o, rc);
+    put<int>(o, (int)err.size());
+    std::fwrite(err.data(), 1, err.size(), o);
+    put<int>(o, canonical ? 1 : 0);
+    std::fclose(o);
+    return 0;
+  }
 
   lpop::HostLayout lay;
   std::string err;

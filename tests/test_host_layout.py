@@ -243,6 +243,70 @@ def test_invalid_input_names_the_first_offending_entry(runner, tmp_path, what, e
     assert lay["rc"] < 0 and lay["err"] == expect
 
 
+def run_validate(runner, tmp_path, m, n, rp, ci, v):
+    pre = str(tmp_path / "val_")
+    np.asarray(rp, np.int64).tofile(pre + "rp.bin")
+    np.asarray(ci, np.int32).tofile(pre + "ci.bin")
+    np.asarray(v, np.float64).tofile(pre + "v.bin")
+    out = str(tmp_path / "val_out.bin")
+    subprocess.run([runner, str(m), str(n), str(len(ci)), pre, out, "0", "0", "-1"], check=True)
+    d = open(out, "rb").read()
+    rc, n_err = np.frombuffer(d[:8], "<i4")
+    err = d[8:8 + n_err].decode()
+    return int(rc), err, bool(np.frombuffer(d[8 + n_err:12 + n_err], "<i4")[0])
+
+
+def test_validation_on_host_threads_matches_its_definition(runner, tmp_path):
+    """validate_csr on a matrix large enough to be split over host threads
+    (>= 2^16 entries, many empty rows): the first entry with a column out of
+    range or a non-finite value is the one named, the first decreasing row
+    pointer is the one named, and the canonical flag (every row strictly
+    increasing in column) is decided by the rows alone, whatever the columns
+    on either side of a row start."""
+    rng = np.random.default_rng(11)
+    m, n = 60000, 5000
+    lens = rng.integers(0, 9, m) * (rng.random(m) < 0.7)
+    rows = [np.sort(rng.choice(n, size=k, replace=False)) for k in lens]
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    ci = np.concatenate(rows).astype(np.int32)
+    v = rng.standard_normal(len(ci))
+    nnz = len(ci)
+    assert nnz >= 1 << 17
+    starts = rp[1:-1][(rp[1:-1] > 0) & (rp[1:-1] < nnz)]
+    assert np.any(ci[starts - 1] >= ci[starts])  # descents across row starts exist
+    assert run_validate(runner, tmp_path, m, n, rp, ci, v) == (0, "", True)
+
+    multi = np.flatnonzero(lens >= 2)
+    for r in (multi[0], multi[len(multi) // 2], multi[-1]):  # one descent or one repeat in one row
+        for kind in ("swap", "repeat"):
+            c = ci.copy()
+            k = rp[r]
+            if kind == "swap":
+                c[k], c[k + 1] = c[k + 1], c[k]
+            else:
+                c[k + 1] = c[k]
+            assert run_validate(runner, tmp_path, m, n, rp, c, v) == (0, "", False), (r, kind)
+
+    for ks, kv, want in (((nnz - 5, nnz // 2), (), "col_idx[%d] out of range" % (nnz // 2)),
+                         ((nnz // 4 + 1,), (3 * nnz // 4,), "col_idx[%d] out of range" % (nnz // 4 + 1)),
+                         ((nnz - 1,), (nnz // 3, nnz - 2), "val[%d] is not finite" % (nnz // 3))):
+        c, w = ci.copy(), v.copy()
+        for k in ks:
+            c[k] = n if k % 2 else -7
+        for k in kv:
+            w[k] = np.inf if k % 2 else np.nan
+        rc, err, _ = run_validate(runner, tmp_path, m, n, rp, c, w)
+        assert rc < 0 and err == want
+
+    p = rp.copy()
+    nz = np.flatnonzero(lens > 0)
+    r1, r2 = nz[len(nz) // 2], nz[-3]
+    p[r1 + 1] = p[r1] - 1
+    p[r2 + 1] = p[r2] - 1
+    rc, err, _ = run_validate(runner, tmp_path, m, n, p, ci, v)
+    assert rc < 0 and err == "row_ptr must be non-decreasing (row %d)" % r1
+
+
 def test_empty_rows_and_no_constraints(runner, tmp_path):
     lay = run_layout(runner, tmp_path, 0, 5, [0], [], [])
     assert lay["rc"] == 0 and lay["nnz"] == 0 and sorted(lay["pcol"]) == list(range(5))
