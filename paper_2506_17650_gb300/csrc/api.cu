@@ -743,19 +743,22 @@ int create_impl(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const
   if (m < 0 || n < 1) return set_err(nullptr, LP_ERR_INVALID_ARG, "need m >= 0 and n >= 1");
   if ((m > 0 && (!b || !sense)) || !c || !lb || !ub)
     return set_err(nullptr, LP_ERR_INVALID_ARG, "b, c, lb, ub and sense must not be NULL");
-  // the first offending row, then the first offending column (on host threads)
-  auto bad_row = [&](long long i) {
-    return !std::isfinite(b[i]) || (sense[i] != 'E' && sense[i] != 'L' && sense[i] != 'G');
+  // the first offending row, then the first offending column (on host
+  // threads; the tests are combined with | so that a scan has no branches)
+  auto bad_row = [&](long long i) -> bool {
+    const char sn = sense[i];
+    return !std::isfinite(b[i]) | ((sn != 'E') & (sn != 'L') & (sn != 'G'));
   };
-  auto bad_bounds = [&](long long j) {
-    return std::isnan(lb[j]) || std::isnan(ub[j]) || lb[j] == INFINITY || ub[j] == -INFINITY || lb[j] > ub[j];
+  auto bad_bounds = [&](long long j) -> bool {
+    const double l = lb[j], u = ub[j];
+    return std::isnan(l) | std::isnan(u) | (l == INFINITY) | (u == -INFINITY) | (l > u);
   };
   const long long i0 = first_bad_index(m, bad_row);
   if (i0 < m) {
     if (!std::isfinite(b[i0])) return set_err(nullptr, LP_ERR_INVALID_INPUT, "b[" + std::to_string(i0) + "] is not finite");
     return set_err(nullptr, LP_ERR_INVALID_INPUT, "sense[" + std::to_string(i0) + "] must be 'E', 'L' or 'G'");
   }
-  const long long j0 = first_bad_index(n, [&](long long j) { return !std::isfinite(c[j]) || bad_bounds(j); });
+  const long long j0 = first_bad_index(n, [&](long long j) -> bool { return !std::isfinite(c[j]) | bad_bounds(j); });
   if (j0 < n) {
     if (!std::isfinite(c[j0])) return set_err(nullptr, LP_ERR_INVALID_INPUT, "c[" + std::to_string(j0) + "] is not finite");
     return set_err(nullptr, LP_ERR_INVALID_INPUT,

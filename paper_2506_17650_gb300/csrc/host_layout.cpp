@@ -156,18 +156,8 @@ long long sliced_entries(const BinTable& bt) {
   return total;
 }
 
-long long first_bad_index(long long count, const std::function<bool(long long)>& bad) {
-  std::mutex mu;
-  long long first = count;
-  parallel_ranges(count, [&](long long b, long long e) {
-    long long i = b;
-    while (i < e && !bad(i)) ++i;
-    if (i < e) {
-      std::lock_guard<std::mutex> lock(mu);
-      first = std::min(first, i);
-    }
-  });
-  return first;
+void for_each_range(long long count, const std::function<void(long long, long long)>& fn, long long work) {
+  parallel_ranges(count, fn, work);
 }
 
 int validate_csr(int32_t m, int32_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,

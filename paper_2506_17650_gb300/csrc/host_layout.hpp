@@ -5,7 +5,9 @@
 
 #include <stdint.h>
 
+#include <algorithm>
 #include <functional>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -22,9 +24,29 @@ struct HostLayout {
   BinTable binsA{}, binsAt{};
 };
 
+// fn(begin, end) over [0, count) in contiguous pieces, on the layout's host
+// threads when the work (count, or `work` when given) is large.
+void for_each_range(long long count, const std::function<void(long long, long long)>& fn, long long work = -1);
+
 // Smallest i in [0, count) with bad(i), or count if there is none; on the
-// layout's host threads when count is large.
-long long first_bad_index(long long count, const std::function<bool(long long)>& bad);
+// layout's host threads when count is large.  A piece is first tested whole
+// (bad ORed over it without an early exit, so the loop has no branch to
+// mispredict) and walked for its first bad index only when it holds one.
+template <class Bad>
+long long first_bad_index(long long count, Bad bad) {
+  std::mutex mu;
+  long long first = count;
+  for_each_range(count, [&](long long b, long long e) {
+    bool any = false;
+    for (long long i = b; i < e; ++i) any |= bad(i);
+    if (!any) return;
+    long long i = b;
+    while (!bad(i)) ++i;
+    std::lock_guard<std::mutex> lock(mu);
+    first = std::min(first, i);
+  });
+  return first;
+}
 
 // Check a caller's CSR matrix: sizes and pointers, row_ptr (0 first, nnz
 // last, non-decreasing), then every entry (column in range, finite value),

@@ -126,3 +126,42 @@ def test_no_gpu_reports_cuda_error():
     lpbuild.build()
     lp = lpgen.mixed_small(0, m=12, n=20)
     _expect(lpop.LP_ERR_CUDA, lp)
+
+
+@pytest.mark.parametrize("what", ["b_inf_two", "sense_two", "c_nan_then_bounds", "bounds_two"])
+def test_large_vectors_name_the_first_offending_entry(lib, what):
+    """The vector checks run over ranges on host threads (n = 200,000 here):
+    with two offending entries in different ranges the first one is named."""
+    lp = lpgen.transport(0)
+    lp.b = lp.b.copy(); lp.c = lp.c.copy(); lp.sense = lp.sense.copy(); lp.lb = lp.lb.copy(); lp.ub = lp.ub.copy()
+    m, n = lp.m, lp.n
+    if what == "b_inf_two":
+        lp.b[m - 3] = -math.inf
+        lp.b[m // 2 + 1] = math.inf
+        want = "b[%d] is not finite" % (m // 2 + 1)
+    elif what == "sense_two":
+        lp.sense[m - 1] = ord("x")
+        lp.sense[7 * m // 8] = ord("l")
+        want = "sense[%d] must be 'E', 'L' or 'G'" % (7 * m // 8)
+    elif what == "c_nan_then_bounds":
+        lp.c[3 * n // 4] = math.nan
+        lp.lb[n // 3], lp.ub[n // 3] = 5.0, 4.0
+        want = "bounds of variable %d are invalid" % (n // 3)
+    else:
+        lp.ub[n - 2] = -math.inf
+        lp.lb[n // 5 + 3] = math.nan
+        want = "bounds of variable %d are invalid" % (n // 5 + 3)
+    msg = _expect(lpop.LP_ERR_INVALID_INPUT, lp)
+    assert want in msg, msg
+
+
+def test_large_valid_input_passes_the_host_checks():
+    """A valid LP large enough for the threaded checks gets past every host
+    check: without a GPU lp_create then fails at the device, not on input."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lpbuild.build()
+    lp = lpgen.transport(0)
+    assert lp.n > 1 << 16
+    _expect(lpop.LP_ERR_CUDA, lp)
