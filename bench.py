@@ -575,7 +575,6 @@ def gpu_arm(args):
             extra["fixed_precond"] = {"alpha": 0.0, "attempts": fr[-1][1]["iterations"],
                                       "time_to_tol_ms": statistics.median(r[0] for r in fr),
                                       "iters_per_s": sum(r[1]["iterations"] for r in fr) / (sum(r[0] for r in fr) / 1e3)}
-            extra["e2e"] = end_to_end(lpop, lp, opts, tol, iter_limit, steps=3)
             _, x, y = budget_run(lpop, torch, prob, stream, TOL, 1_000_000, kkt_dir, "fp64")
 
     cpu = None
@@ -596,11 +595,11 @@ def gpu_arm(args):
         elif "fp64" in kkts:
             k = kkts["fp64"]
             extra["oracle_kkt_of_returned_point"] = max(k["rel_pres"], k["rel_dres"], k["rel_gap"])
-    if rank == 0 and large:
+    if rank == 0:
         # after the oracle child has exited, so that lp_create's host work (the
         # CSR checks on host threads) and the pinned copies have the host cores
         # to themselves, as a caller's would
-        extra["e2e"] = end_to_end(lpop, lp, opts, tol, iter_limit, steps=2)
+        extra["e2e"] = end_to_end(lpop, lp, opts, tol, iter_limit, steps=2 if large else 3)
 
     if rank == 0:
         step_desc = (f"{STEP_ATTEMPTS} step attempts from the initial point (ten check periods: KKT checks, "
